@@ -1,0 +1,364 @@
+"""Pins of the FP64 CPU oracle to what the paper and the mathematics fix.
+
+None of these compare the oracle with a retyped copy of its own formulas:
+each checks a property that a dropped term, a wrong sign, a wrong velocity
+numbering or a transposed operand would break (moment identities of Sec. III,
+closed forms of the double well, stencil reductions of Sec. II, exact fixed
+points, lattice symmetry, the discrete equilibrium of Sec. I solved without
+the LBE, and the steady-state relations of Sec. II).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import equilibrium as eq
+from oracle.oracle import CX, CY, STANDARD, WELL_BALANCED, W, Oracle, Params
+
+CS2 = 1.0 / 3.0
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def _params(nx=1, ny=21, scheme=WELL_BALANCED, tau=0.8, kappa=0.01, width=4.0,
+            rho_l=1.0, rho_g=0.1, rho0=0.0, beta=None):
+    if beta is None:
+        beta = eq.beta_for_width(kappa, width, rho_l, rho_g)
+    return Params(nx, ny, tau, kappa, beta, rho_l, rho_g, rho0, scheme)
+
+
+def _slab(ny, width=4.0, rho_l=1.0, rho_g=0.1, half=None):
+    """Liquid outside |y| < half (minimum image about y = 0), symmetric
+    under y -> -y."""
+    y = np.arange(ny, dtype=float)
+    d = np.minimum(y, ny - y)
+    half = ny / 4 if half is None else half
+    return 0.5 * (rho_l + rho_g) + 0.5 * (rho_l - rho_g) * np.tanh(2 * (d - half) / width)
+
+
+def _moments(vec):
+    """Zeroth to third moments of a 9-vector over the D2Q9 set."""
+    c = np.array([CX, CY], dtype=float)           # (2, 9)
+    m0 = vec.sum()
+    m1 = c @ vec
+    m2 = np.einsum("ai,bi,i->ab", c, c, vec)
+    m3 = np.einsum("ai,bi,gi,i->abg", c, c, c, vec)
+    return m0, m1, m2, m3
+
+
+def _uI(u):
+    d = np.eye(2)
+    return (np.einsum("a,bg->abg", u, d) + np.einsum("b,ag->abg", u, d)
+            + np.einsum("g,ab->abg", u, d))
+
+
+# ---- free energy (Eq. doubleWell, Eq. EOS) -------------------------------------
+
+def test_mu0_is_derivative_of_psi0_and_wells_are_coexistence():
+    o = Oracle(_params())
+    p = o.p
+    for rho in np.linspace(0.05, 1.2, 23):
+        h = 1e-5
+        fd = (o.psi0(rho + h) - o.psi0(rho - h)) / (2 * h)
+        assert abs(o.mu0(rho) - fd) < 1e-9
+    # both saturation densities: mu0 = 0 and p0 = 0 (common tangent)
+    for rho in (p.rho_l, p.rho_g):
+        assert abs(o.mu0(rho)) < 1e-16
+        assert abs(o.p0(rho)) < 1e-16
+    # p0 = rho mu0 - psi0 is the Legendre transform: dp0/drho = rho dmu0/drho
+    rho, h = 0.43, 1e-5
+    dp = (o.p0(rho + h) - o.p0(rho - h)) / (2 * h)
+    dmu = (o.mu0(rho + h) - o.mu0(rho - h)) / (2 * h)
+    assert abs(dp - rho * dmu) < 1e-9
+
+
+# ---- moment identities of the equilibria and forcing terms (Sec. II, III) -------
+
+@pytest.mark.parametrize("rho0", [0.0, 0.37])
+def test_well_balanced_moment_identities(rho0):
+    rng = np.random.default_rng(11)
+    o = Oracle(_params(scheme=WELL_BALANCED, rho0=rho0))
+    for _ in range(50):
+        rho = rng.uniform(0.05, 1.2)
+        u = rng.uniform(-0.1, 0.1, 2)
+        F = rng.uniform(-0.05, 0.05, 2)
+        gr = rng.uniform(-0.3, 0.3, 2)
+        m0, m1, m2, m3 = _moments(o.feq(rho, *u))
+        assert m0 == pytest.approx(rho, abs=1e-15)
+        np.testing.assert_allclose(m1, rho * u, atol=1e-16)
+        # sum c c f^eq = rho u u, plus the isotropic constant cs^2 rho0 I the
+        # rest weights of rho0 carry (zero for the paper's rho0 = 0)
+        np.testing.assert_allclose(m2, rho * np.outer(u, u) + CS2 * rho0 * np.eye(2), atol=1e-16)
+        np.testing.assert_allclose(m3, CS2 * rho * _uI(u), atol=1e-16)
+        g0, g1, g2, _ = _moments(o.forcing(*u, *F, *gr))
+        assert abs(g0) < 1e-16
+        np.testing.assert_allclose(g1, F, atol=1e-16)
+        uF = np.outer(u, F) + np.outer(F, u)
+        ugr = np.outer(u, gr) + np.outer(gr, u)
+        np.testing.assert_allclose(g2, uF + CS2 * (ugr + np.dot(u, gr) * np.eye(2)), atol=1e-16)
+
+
+def test_standard_moment_identities():
+    rng = np.random.default_rng(12)
+    o = Oracle(_params(scheme=STANDARD))
+    for _ in range(50):
+        rho = rng.uniform(0.05, 1.2)
+        u = rng.uniform(-0.1, 0.1, 2)
+        F = rng.uniform(-0.05, 0.05, 2)
+        m0, m1, m2, m3 = _moments(o.feq(rho, *u))
+        assert m0 == pytest.approx(rho, abs=1e-15)
+        np.testing.assert_allclose(m1, rho * u, atol=1e-16)
+        np.testing.assert_allclose(m2, rho * np.outer(u, u) + CS2 * rho * np.eye(2), atol=1e-15)
+        np.testing.assert_allclose(m3, CS2 * rho * _uI(u), atol=1e-16)
+        g0, g1, g2, _ = _moments(o.forcing(*u, *F))
+        assert abs(g0) < 1e-16
+        np.testing.assert_allclose(g1, F, atol=1e-16)
+        np.testing.assert_allclose(g2, np.outer(u, F) + np.outer(F, u), atol=1e-16)
+
+
+def test_well_balanced_rest_state_has_no_lattice_pressure():
+    """Eq. mFeq at u = 0: all of rho sits in f_0 except the constant rho0
+    weights, so the ideal-gas term that streaming would turn into
+    grad(cs^2 rho) is absent (Sec. III)."""
+    o = Oracle(_params(scheme=WELL_BALANCED, rho0=0.25))
+    feq = o.feq(0.7, 0.0, 0.0)
+    assert feq[0] == pytest.approx(0.7 - (1 - W[0]) * 0.25, abs=1e-16)
+    np.testing.assert_allclose(feq[1:], np.array(W[1:]) * 0.25, atol=1e-17)
+
+
+# ---- stencils (Sec. II) --------------------------------------------------------
+
+def test_gradient_and_laplacian_exact_on_quadratics():
+    nx, ny = 13, 11
+    o = Oracle(_params(nx=nx, ny=ny))
+    x = np.arange(nx, dtype=float)[None, :]
+    y = np.arange(ny, dtype=float)[:, None]
+    a = np.array([0.3, -0.7, 1.1, 0.05, -0.02, 0.013])
+    phi = a[0] + a[1] * x + a[2] * y + a[3] * x * x + a[4] * x * y + a[5] * y * y
+    gx, gy = o.gradient(phi)
+    lap = o.laplacian(phi)
+    inner = (slice(1, ny - 1), slice(1, nx - 1))      # away from the periodic seam
+    np.testing.assert_allclose(gx[inner], (a[1] + 2 * a[3] * x + a[4] * y + 0 * y)[inner], atol=1e-13)
+    np.testing.assert_allclose(gy[inner], (a[2] + a[4] * x + 2 * a[5] * y + 0 * x)[inner], atol=1e-13)
+    np.testing.assert_allclose(lap[inner], np.full((ny - 2, nx - 2), 2 * a[3] + 2 * a[5]), atol=1e-13)
+
+
+def test_stencils_reduce_to_paper_1d_forms_and_taylor_errors():
+    """Sec. II: in 1D the ICS gradient is (rho_{j+1} - rho_{j-1})/2 and the
+    force-side composite (d_{j+1} + 2 d_j + d_{j-1})/4 of it carries the
+    truncation error (5/12) d^3 rho, against 1/6 for the central difference."""
+    ny, nx = 400, 3
+    o = Oracle(_params(nx=nx, ny=ny))
+    k = 2 * np.pi / ny * 3
+    y = np.arange(ny, dtype=float)
+    rho1 = 0.5 + 0.2 * np.sin(k * y)
+    rho = np.repeat(rho1[:, None], nx, axis=1)
+    gx, gy = o.gradient(rho)
+    lap = o.laplacian(rho)
+    np.testing.assert_allclose(gy[:, 1], 0.5 * (np.roll(rho1, -1) - np.roll(rho1, 1)), atol=1e-15)
+    np.testing.assert_allclose(gx, 0.0, atol=1e-15)
+    np.testing.assert_allclose(lap[:, 1], np.roll(rho1, -1) - 2 * rho1 + np.roll(rho1, 1), atol=1e-15)
+    d = gy[:, 1]
+    dF = 0.25 * (np.roll(d, -1) + 2 * d + np.roll(d, 1))
+    d1 = 0.2 * k * np.cos(k * y)
+    d3 = -0.2 * k ** 3 * np.cos(k * y)
+    # residuals after removing the stated leading error are O(k^5)
+    assert np.max(np.abs(dF - d1 - 5.0 / 12.0 * d3)) < 5 * 0.2 * k ** 5
+    assert np.max(np.abs(d - d1 - 1.0 / 6.0 * d3)) < 5 * 0.2 * k ** 5
+    assert np.max(np.abs(dF - d - 1.0 / 4.0 * d3)) < 5 * 0.2 * k ** 5
+
+
+# ---- exact invariants of the update ---------------------------------------------
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+@pytest.mark.parametrize("rho0", [0.0, 0.4])
+def test_uniform_rest_state_is_a_fixed_point(scheme, rho0):
+    o = Oracle(_params(nx=5, ny=4, scheme=scheme, rho0=rho0))
+    f = o.init(np.full((4, 5), 0.63))
+    f0 = f.copy()
+    o.step(f, 7)
+    np.testing.assert_allclose(f, f0, atol=1e-14, rtol=0)   # a few ulps: rho = sum f_i is rounded
+
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_uniform_flow_is_preserved(scheme):
+    """Uniform rho gives grad rho = grad mu = 0, so F = 0, and f^eq(rho, u0)
+    is invariant under collision and streaming (first moment of Eq. rhoU)."""
+    nx, ny, u0 = 6, 5, (0.05, -0.03)
+    o = Oracle(_params(nx=nx, ny=ny, scheme=scheme))
+    fe = o.feq(0.8, *u0)
+    f = np.empty((9, ny, nx))
+    f[:] = fe[:, None, None]
+    o.step(f, 10)
+    m = o.macro(f)
+    np.testing.assert_allclose(m["ux"], u0[0], atol=1e-15)
+    np.testing.assert_allclose(m["uy"], u0[1], atol=1e-15)
+    np.testing.assert_allclose(f, np.broadcast_to(fe[:, None, None], f.shape), atol=1e-15)
+
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_mass_is_conserved(scheme):
+    from paper_2012_11075_gb300 import workloads as wl
+    pr = wl.droplet(n=24, radius=7.0, rho_g=0.2, tau=0.85)
+    rng = np.random.default_rng(3)
+    rho = pr.rho * (1 + 0.01 * rng.uniform(-1, 1, pr.rho.shape))
+    o = Oracle(_params(nx=24, ny=24, scheme=scheme, tau=0.85, rho_g=0.2))
+    f = o.init(rho)
+    m0 = o.stats(f)["mass"]
+    o.step(f, 1000)
+    st = o.stats(f)
+    assert not st["nonfinite"]
+    assert abs(st["mass"] - m0) / m0 < 1e-13
+
+
+def _mirror_x(a):
+    """a(x) -> a(-x mod n) along the last axis."""
+    return np.roll(a[..., ::-1], 1, axis=-1)
+
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_lattice_symmetry_equivariance(scheme):
+    """The D2Q9 update commutes with the lattice symmetries: reflecting
+    x -> -x or exchanging x and y in the initial density reflects or exchanges
+    the whole solution (u_x changes sign / u_x and u_y swap)."""
+    n = 16
+    from paper_2012_11075_gb300 import workloads as wl
+    rng = np.random.default_rng(5)
+    rho = wl.droplet_field(n, n, [(5.3, 7.1)], [4.5], 1.0, 0.2, 4.0)
+    rho = rho * (1 + 0.02 * rng.uniform(-1, 1, rho.shape))
+    o = Oracle(_params(nx=n, ny=n, scheme=scheme, tau=0.85, rho_g=0.2))
+    steps = 60
+
+    def run(r):
+        f = o.init(np.ascontiguousarray(r))
+        o.step(f, steps)
+        return o.macro(f)
+
+    base = run(rho)
+    mir = run(_mirror_x(rho))
+    np.testing.assert_allclose(mir["rho"], _mirror_x(base["rho"]), atol=1e-12)
+    np.testing.assert_allclose(mir["ux"], -_mirror_x(base["ux"]), atol=1e-12)
+    np.testing.assert_allclose(mir["uy"], _mirror_x(base["uy"]), atol=1e-12)
+    tr = run(rho.T)
+    np.testing.assert_allclose(tr["rho"], base["rho"].T, atol=1e-12)
+    np.testing.assert_allclose(tr["ux"], base["uy"].T, atol=1e-12)
+    np.testing.assert_allclose(tr["uy"], base["ux"].T, atol=1e-12)
+    assert np.max(np.abs(base["ux"])) > 1e-6          # the case is not trivial
+
+
+# ---- the discrete equilibrium state S = {mu = const, u = 0} (Sec. I, III) ---------
+
+def test_well_balanced_flat_interface_reaches_discrete_equilibrium():
+    """A WB run from the tanh profile converges to the fixed-mass solution of
+    mu_0(rho_j) - kappa lap_h rho_j = const found by Newton's method without
+    the LBE.  Odd lattice: on even ones the balance of Sec. III also admits
+    an alternating mode rho_j d_h mu_j = a (-1)^j."""
+    ny = 21
+    p = _params(nx=1, ny=ny, scheme=WELL_BALANCED, tau=0.8)
+    rho_init = _slab(ny)[:, None].copy()
+    o = Oracle(p)
+    f = o.init(rho_init)
+    o.step(f, 50000)
+    st = o.stats(f)
+    m = o.macro(f)
+    rN, mu_bar = eq.discrete_flat_equilibrium(rho_init[:, 0], p.kappa, p.beta, p.rho_l, p.rho_g)
+    assert st["umax"] < 1e-13
+    assert st["mu_max"] - st["mu_min"] < 1e-13
+    assert np.max(np.abs(m["rho"][:, 0] - rN)) < 1e-10
+    assert np.max(np.abs(m["mu"] - mu_bar)) < 1e-13
+
+
+def test_equilibrium_profile_is_fixed_point_of_wb_not_of_standard():
+    """Start both schemes from the discrete equilibrium of a wide slab at the
+    paper's parameters (rho_v = 0.2, beta = 0.01, kappa = 0.0128, tau = 0.85).
+    WB keeps it (u at round-off) and its bulk densities are the double-well
+    minima; the standard scheme leaves it (Sec. II: S does not solve its
+    discrete balance)."""
+    ny = 201
+    beta, kappa, rl, rg = 0.01, 0.0128, 1.0, 0.2
+    width = eq.interface_width(kappa, beta, rl, rg)
+    assert width == pytest.approx(4.0)
+    rho_init = _slab(ny, width=width, rho_l=rl, rho_g=rg, half=50.0)
+    rN, _ = eq.discrete_flat_equilibrium(rho_init, kappa, beta, rl, rg)
+    # bulk values of the discrete equilibrium are the coexistence densities
+    assert abs(rN[100] - rl) < 1e-12 and abs(rN[0] - rg) < 1e-12
+    out = {}
+    for scheme in (WELL_BALANCED, STANDARD):
+        p = Params(1, ny, 0.85, kappa, beta, rl, rg, 0.0, scheme)
+        o = Oracle(p)
+        f = o.init(rN[:, None].copy())
+        o.step(f, 2000)
+        out[scheme] = (o.stats(f), o.macro(f))
+    st, m = out[WELL_BALANCED]
+    assert st["umax"] < 1e-14
+    assert np.max(np.abs(m["rho"][:, 0] - rN)) < 1e-13
+    st_s, m_s = out[STANDARD]
+    assert st_s["umax"] > 1e-6
+    assert np.max(np.abs(m_s["rho"][:, 0] - rN)) > 1e-5
+
+
+def test_standard_steady_state_satisfies_paper_balance():
+    """At the standard scheme's 1D steady state the closed forms of Sec. II
+    hold: f_A = (2/3) rho (1 - v^2/(2 cs^2)) + (1/3)(1 - 2 tau) v F / cs^2,
+    f_B - f_C = rho v - F/2, f_B + f_C = rho - f_A, and the discrete momentum
+    balance Eq. momentumBalance with R(v) of Eq. Rv."""
+    ny, tau = 101, 0.85
+    beta, kappa, rl, rg = 0.01, 0.0128, 1.0, 0.2
+    width = eq.interface_width(kappa, beta, rl, rg)
+    y = np.arange(ny, dtype=float)
+    rho = eq.tanh_slab(y, 25, 75, width, rl, rg)[:, None].copy()
+    p = Params(1, ny, tau, kappa, beta, rl, rg, 0.0, STANDARD)
+    o = Oracle(p)
+    f = o.init(rho)
+    o.step(f, 40000)
+    m = o.macro(f)
+    r, v, F = m["rho"][:, 0], m["uy"][:, 0], m["Fy"][:, 0]
+    fA = f[0, :, 0] + f[1, :, 0] + f[3, :, 0]
+    fB = f[2, :, 0] + f[5, :, 0] + f[6, :, 0]
+    fC = f[4, :, 0] + f[7, :, 0] + f[8, :, 0]
+    np.testing.assert_allclose(fA, 2 / 3 * r * (1 - v * v / (2 * CS2)) + (1 - 2 * tau) * v * F / (3 * CS2), atol=1e-14)
+    np.testing.assert_allclose(fB - fC, r * v - 0.5 * F, atol=1e-14)
+    np.testing.assert_allclose(fB, r / 6 + r * v / 2 + r * v * v / 2 - F / 4 + (tau - 0.5) * F * v, atol=1e-14)
+    rp, rm_ = np.roll(r, -1), np.roll(r, 1)
+    Fp, Fm = np.roll(F, -1), np.roll(F, 1)
+    vp, vm = np.roll(v, -1), np.roll(v, 1)
+    R = ((rp * vp - 2 * r * v + rm_ * vm) / 2 + (2 * tau - 1) * (Fp * vp - Fm * vm) / 2
+         + (rp * vp * vp - rm_ * vm * vm) / 2)
+    lhs = -CS2 * (rp - rm_) / 2 + (Fp + 2 * F + Fm) / 4
+    assert np.max(np.abs(F)) > 1e-2                 # the terms are not small
+    np.testing.assert_allclose(lhs, -R, atol=1e-14)
+    # and mu is not uniform: the standard scheme misses S (Sec. IV.A: O(1e-3))
+    assert 1e-4 < m["mu"].max() - m["mu"].min() < 1e-2
+
+
+# ---- the paper's printed results, order of magnitude ----------------------------
+
+def test_paper_flat_interface_orders_of_magnitude():
+    """Sec. IV.A, Fig. 2 and 3.  Standard LBE on the noisy 21 x 101 slab:
+    kinetic energy plateaus near 1e-12, velocity near 1e-8, mu varies at
+    O(1e-3).  WB-LBE on the same slab profile (one column, no noise): kinetic
+    energy falls ten orders below the standard plateau within 30000 steps
+    and mu is uniform to O(1e-8), on its way to the round-off floor (the
+    GPU tests follow it further)."""
+    from paper_2012_11075_gb300 import workloads as wl
+    gold = json.load(open(GOLDEN))["flat_interface"]
+    pr = wl.paper_flat()
+    o = Oracle(Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g, 0.0, STANDARD))
+    f = o.init(pr.rho)
+    o.step(f, 20000)
+    std = o.stats(f)
+    assert 1e-2 * gold["kinetic_energy_standard"] < std["kinetic"] < 1e2 * gold["kinetic_energy_standard"]
+    assert 0.1 * gold["velocity_standard"] < std["umax"] < 10 * gold["velocity_standard"]
+    spread = std["mu_max"] - std["mu_min"]
+    assert 0.1 * gold["mu_variation_standard"] < spread < 10 * gold["mu_variation_standard"]
+
+    width = math.sqrt(8 * pr.kappa / pr.beta) / (pr.rho_l - pr.rho_g)
+    y = np.arange(pr.ny, dtype=float)
+    rho1 = eq.tanh_slab(y, 25, 75, width, pr.rho_l, pr.rho_g)[:, None].copy()
+    o = Oracle(Params(1, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g, 0.0, WELL_BALANCED))
+    f = o.init(rho1)
+    o.step(f, 30000)
+    wb = o.stats(f)
+    assert wb["kinetic"] < 1e-8 * gold["kinetic_energy_standard"]
+    assert wb["mu_max"] - wb["mu_min"] < 1e-7
