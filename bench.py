@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fused well-balanced D2Q9 step on one GB300.
+
+Workload (the large-domain throughput case): a 4096 x 4096 periodic lattice
+with 64 droplets at seeded non-overlapping centres (radii U[16, 64]),
+rho_l = 1, rho_g = 0.1 (density ratio 10), kappa = 0.01, W = 5, tau = 0.7,
+well-balanced scheme.  One benchmark step = S lattice time steps (fused
+collide-stream kernel) followed by one statistics pass (mass, max|u|, mu
+range, kinetic energy, non-finite flag).  The headline is the FP32-shifted
+path; the FP64 path is measured on the same lattice and reported beside it.
+
+`value` is MLUPS (lattice-node updates per second / 1e6) with the state
+resident in HBM; the population buffers (2 x 604 MB in FP32) are larger than
+L2, so no flush is needed between steps.  `e2e` measures the same through the
+C ABI with host buffers: every step copies the initial density in from pinned
+host memory, runs S steps and reads the density field and stats back.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one lattice time step per benchmark step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+import numpy as np
+
+METRIC = "MLUPS and HBM-roofline % (WB D2Q9, FP64 vs FP32); batched solve p50/p99"
+UNIT = "MLUPS"
+WORKLOAD = "large_domain_4096x4096_64droplets_ratio10_wb"
+BYTES_PER_LU = {"f32": 72, "f64": 144}          # 9 reads + 9 writes per node update
+SUBSTEPS = {"f32": 200, "f64": 40}              # lattice steps per benchmark step
+PROFILE_JSON = ROOT / "profiles" / "lbm_step_traffic.json"
+KERNEL_SOURCES = [ROOT / "paper_2012_11075_gb300" / "csrc" / "lbm_kernels.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float, device=None) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_problem():
+    from paper_2012_11075_gb300 import workloads as wl
+    return wl.large_domain(n=4096, count=64, ratio=10.0, width=5.0, kappa=0.01, tau=0.7)
+
+
+# ---------------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    """The oracle, as it stands, on the host cores: one FP64 lattice step of
+    the full 4096^2 lattice per benchmark step."""
+    if rank != 0:
+        return 0
+    from oracle.oracle import Oracle, Params as OParams
+    pr = make_problem()
+    o = Oracle(OParams(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g, 0.0, 1))
+    f = o.init(pr.rho)
+    for _ in range(args.warmup):
+        o.step(f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(f, 1)
+    dt = time.perf_counter() - t0
+    mlups = pr.nx * pr.ny * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "lattice_steps_per_step": 1,
+                   "scheme": "well_balanced", "precision": "fp64"},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} FP64 lattice steps of the full {pr.nx}x{pr.ny} lattice, single thread"},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(pr, seconds_target=15.0):
+    """Oracle MLUPS on the host (one thread) on a bounded sample: full lattice,
+    as many FP64 steps as fit in about seconds_target (at least one)."""
+    from oracle.oracle import Oracle, Params as OParams
+    o = Oracle(OParams(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g, 0.0, 1))
+    f = o.init(pr.rho)
+    t0 = time.perf_counter()
+    o.step(f, 1)
+    dt1 = time.perf_counter() - t0
+    n = max(1, min(5, int(seconds_target / max(dt1, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    o.step(f, n)
+    dt = time.perf_counter() - t0
+    return {"value": pr.nx * pr.ny * n / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} FP64 lattice steps (after 1 untimed) of the full {pr.nx}x{pr.ny} lattice, single thread"}
+
+
+def time_device(solver, substeps, steps, warmup, stream, torch):
+    """Device-resident timing: K x (S lattice steps + stats pass).  Returns
+    total seconds, seconds in the step kernels, launches."""
+    for _ in range(warmup):
+        solver.step(substeps)
+        solver.stats()
+    torch.cuda.synchronize()
+    l0 = solver.kernel_launches
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            solver.step(substeps)
+            ev[2 * k + 1].record(stream)
+            solver.stats()                      # synchronises: the step's result
+            ev[2 * k + 2].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[-1]) / 1e3
+    kern = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)) / 1e3
+    return total, kern, solver.kernel_launches - l0
+
+
+def time_e2e(solver, rho_pinned, rho_out_pinned, substeps, steps, warmup, torch):
+    """End to end through the C ABI with host buffers."""
+    for _ in range(warmup):
+        solver.init_rho(rho_pinned)
+        solver.step(substeps)
+        solver.moments_into(rho=rho_out_pinned)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        solver.init_rho(rho_pinned)
+        solver.step(substeps)
+        solver.moments_into(rho=rho_out_pinned)
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2012_11075_gb300 import wblbe
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pr = make_problem()
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_note = "of measured" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or 6800.0
+    stream = torch.cuda.Stream(device=dev)
+    results = {}
+    for prec_name, prec in (("f32", wblbe.FP32_SHIFTED), ("f64", wblbe.FP64)):
+        params = wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g,
+                              scheme=wblbe.WELL_BALANCED, precision=prec)
+        solver = wblbe.Solver(params, stream=stream)
+        solver.init_rho(pr.rho)
+        S = SUBSTEPS[prec_name]
+        K = args.steps if prec_name == "f32" else max(1, min(args.steps, 5))
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            total, kern, launches = time_device(solver, S, K, args.warmup, stream, torch)
+        total = max_over_ranks(world, total, dev)
+        st = solver.stats()
+        lu = pr.nx * pr.ny * S * K
+        step_launches = S * K
+        kern_avg = kern / step_launches
+        achieved_gbs = BYTES_PER_LU[prec_name] * pr.nx * pr.ny / kern_avg / 1e9
+        results[prec_name] = dict(
+            mlups=lu * world / total / 1e6, total=total, kern_avg=kern_avg,
+            achieved_gbs=achieved_gbs, launches=launches, clocks=clk.summary(),
+            launch=solver.get_launch(), umax=st["umax"], mass_drift=st["mass_drift_rel"],
+            nonfinite=st["nonfinite"], S=S, K=K)
+        if prec_name == "f32":
+            rho_pinned = torch.from_numpy(pr.rho).pin_memory()
+            rho_out = torch.empty_like(rho_pinned).pin_memory()
+            e2e_t = time_e2e(solver, rho_pinned, rho_out, S, K, min(args.warmup, 2), torch)
+            e2e_t = max_over_ranks(world, e2e_t, dev)
+            results["e2e"] = dict(mlups=lu * world / e2e_t / 1e6, seconds=e2e_t,
+                                  h2d=pr.nx * pr.ny * 8, d2h=pr.nx * pr.ny * 8 + 6 * 8)
+        solver.close()
+        del solver
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return 0
+    r32, r64 = results["f32"], results["f64"]
+    traffic = None
+    if PROFILE_JSON.exists():
+        prof = json.loads(PROFILE_JSON.read_text())
+        if prof.get("kernel_hash") == kernel_hash():
+            traffic = prof.get("dram_bytes_per_launch_full_size")
+    fp64_peak_tflops = 1.25                       # nominal GB300 FP64 rate (recipe table)
+    fp64_flops_per_lu = 150                       # FP64 instructions per node update, counted
+    line = {
+        "metric": METRIC, "value": r32["mlups"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r32["total"] / r32["K"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "droplets": 64,
+                   "ratio": 10, "tau": pr.tau, "kappa": pr.kappa, "width": 5,
+                   "scheme": "well_balanced", "precision": "fp32_shifted",
+                   "lattice_steps_per_step": r32["S"], "tile_x": r32["launch"][0],
+                   "rows_per_cta": r32["launch"][1],
+                   "l2": "state (2 x 604 MB) larger than L2; no flush",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": r32["achieved_gbs"], "peak": hbm_peak,
+                     "unit": "GB/s", "frac": r32["achieved_gbs"] / hbm_peak,
+                     "traffic": traffic, "peak_source": peak_note,
+                     "bytes_per_lattice_update": BYTES_PER_LU["f32"],
+                     "kernel": "lbm_strip_kernel<float, WB>",
+                     "kernel_ms": r32["kern_avg"] * 1e3},
+        "e2e": {"value": results["e2e"]["mlups"], "unit": UNIT,
+                "h2d_bytes_per_step": results["e2e"]["h2d"],
+                "d2h_bytes_per_step": results["e2e"]["d2h"]},
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+        "fp64": {"value": r64["mlups"], "unit": UNIT, "lattice_steps_per_step": r64["S"],
+                 "steps": r64["K"],
+                 "roofline_hbm": {"achieved": r64["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": r64["achieved_gbs"] / hbm_peak},
+                 "roofline_alu": {"bound": "alu", "achieved": r64["mlups"] * 1e6 * fp64_flops_per_lu / 1e12,
+                                  "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                                  "frac": r64["mlups"] * 1e6 * fp64_flops_per_lu / 1e12 / fp64_peak_tflops},
+                 "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
+        "health": {"f32_umax": r32["umax"], "f32_mass_drift_rel": r32["mass_drift"],
+                   "f64_umax": r64["umax"], "f64_mass_drift_rel": r64["mass_drift"],
+                   "nonfinite": bool(r32["nonfinite"] or r64["nonfinite"])},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_sample(pr)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            return run_reference(args, world, rank)
+        return run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * wblbe.h - C ABI of the GB300 (sm_103a) library for the well-balanced
+ * lattice Boltzmann equation of Guo, "Well-balanced lattice Boltzmann
+ * equation for two-phase flows" (arXiv 2012.11075), with the standard LBE of
+ * its Sec. II as the comparison scheme.
+ *
+ * The method (lattice units dx = dt = c = 1, cs^2 = 1/3, periodic D2Q9):
+ *   f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i
+ *                                                             (Eq. D2Q9)
+ *   rho = sum_i f_i,  rho u = sum_i c_i f_i + F/2             (Eq. rhoU)
+ *   mu  = mu_0(rho) - kappa lap(rho),
+ *   mu_0 = d/drho [beta (rho - rho_l)^2 (rho - rho_g)^2]      (Eq. doubleWell)
+ *   well-balanced: f^eq of Eq. mFeq, F = -rho grad(mu) (Eq. mF), F_i of Eq. mFi
+ *   standard:      f^eq of Eq. feq,  F = grad(cs^2 rho) - rho grad(mu)
+ *                  (potential form, Sec. II), F_i of Eq. Fi.
+ * Gradients and the Laplacian are the isotropic central stencils
+ *   grad(phi) = 3 sum_i w_i c_i phi(x + c_i),
+ *   lap(phi)  = 6 sum_i w_i (phi(x + c_i) - phi(x)),
+ * which reduce to the 1D central forms of Sec. II.
+ *
+ * Conventions for every function below:
+ *  - Every call returns a wblbe_status; nothing throws across the ABI.  On a
+ *    non-OK status, wblbe_last_error(h) gives a one-line reason.
+ *  - Handles are not thread-safe: one host thread drives a handle at a time.
+ *  - Scalar fields are row-major [ny][nx] float64 (x fastest); population
+ *    arrays are [9][ny][nx] float64, direction order
+ *    c0=(0,0) c1=(1,0) c2=(0,1) c3=(-1,0) c4=(0,-1) c5=(1,1) c6=(-1,1)
+ *    c7=(-1,-1) c8=(1,-1).  Populations are f_i(x, t): after streaming,
+ *    before collision (the left-hand side of Eq. D2Q9 at time t).
+ *  - Pointers flagged "on_device" are device addresses on the current CUDA
+ *    device; otherwise they are host addresses.  All arrays are owned by the
+ *    caller.  The library allocates no device memory: the caller passes one
+ *    device workspace (for example a torch uint8 tensor) at creation and
+ *    keeps it alive until wblbe_destroy.
+ *  - Work is issued on the stream given at creation.  wblbe_step is
+ *    asynchronous; functions that return data to host memory synchronise the
+ *    stream before returning.
+ */
+#ifndef WBLBE_H
+#define WBLBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wblbe_ctx* wblbe_handle;
+
+typedef enum {
+  WBLBE_OK = 0,
+  WBLBE_EINVAL = 1,        /* bad argument or parameter set                 */
+  WBLBE_ENOMEM = 2,        /* workspace too small / no free slot or budget  */
+  WBLBE_ECUDA = 3,         /* a CUDA runtime call failed                    */
+  WBLBE_EUNSTABLE = 4,     /* a non-finite rho, u or mu was seen            */
+  WBLBE_ETIMEOUT = 5,      /* a bounded device wait gave up                 */
+  WBLBE_ENOTCONVERGED = 6  /* max_steps reached; the state is still valid   */
+} wblbe_status;
+
+/* Scheme: the standard LBE of Sec. II or the well-balanced LBE of Sec. III. */
+enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1 };
+
+/* Storage/arithmetic precision.
+ * WBLBE_FP64: populations stored and updated in float64.
+ * WBLBE_FP32_SHIFTED: populations stored as float32 deviations
+ *   g_i = f_i - s_i from the scheme's rest equilibrium s_i at rho_ref
+ *   (standard: s_i = w_i rho_ref; well-balanced: s_0 = rho_ref - (1-w_0) rho0,
+ *   s_i = w_i rho0), arithmetic in float32, reductions in float64.  The shift
+ *   is exact in real arithmetic: sum_i s_i = rho_ref and a uniform s_i is
+ *   invariant under streaming. */
+enum { WBLBE_FP64 = 0, WBLBE_FP32_SHIFTED = 1 };
+
+/* The paper's statement of the problem (Sec. IV): lattice nx x ny (periodic),
+ * relaxation time tau (> 1/2), interface parameter kappa (>= 0), double-well
+ * height beta (> 0) and saturation densities rho_l > rho_g > 0
+ * (Eq. doubleWell); rho0 is the numerical constant of Eq. mFeq (the paper
+ * uses 0; only the well-balanced scheme reads it); rho_ref is the FP32 shift
+ * density (NaN selects (rho_l + rho_g)/2; ignored in FP64). */
+typedef struct {
+  int32_t nx, ny;
+  double tau, kappa, beta, rho_l, rho_g;
+  double rho0;
+  double rho_ref;
+  int32_t scheme;     /* WBLBE_STANDARD | WBLBE_WELL_BALANCED   */
+  int32_t precision;  /* WBLBE_FP64 | WBLBE_FP32_SHIFTED        */
+} wblbe_params;
+
+/* Diagnostics of Sec. IV computed from the state f(t) at step `step`:
+ * mass = sum rho, its drift relative to the mass after wblbe_init_rho /
+ * wblbe_set_populations, max |u| (u of Eq. rhoU), min and max of mu,
+ * kinetic energy E = 1/2 sum rho |u|^2, and a flag set if any rho, u or mu
+ * was not finite.  All accumulated in float64. */
+typedef struct {
+  int64_t step;
+  double mass, mass_drift_rel, umax, mu_min, mu_max, kinetic;
+  int32_t nonfinite;
+} wblbe_stats;
+
+/* Launch shape of the fused step kernel: tile_x lattice columns per CTA
+ * (32, 64, 128 or 256) and rows_per_cta rows marched by each CTA (>= 1).
+ * Results do not depend on it. */
+typedef struct {
+  int32_t tile_x;
+  int32_t rows_per_cta;
+} wblbe_launch;
+
+/* Device workspace bytes a handle with these parameters needs; 0 if the
+ * parameters are invalid.  Layout: two population buffers, one float64 field
+ * of staging, reduction partials and a stats record, each 256-byte aligned. */
+size_t wblbe_workspace_bytes(const wblbe_params* params);
+
+/* Create a handle.  dev_workspace: device pointer, 256-byte aligned, at
+ * least wblbe_workspace_bytes(params) bytes, borrowed until wblbe_destroy.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The state is
+ * undefined until wblbe_init_rho or wblbe_set_populations.
+ * EINVAL: bad params, NULL out, misaligned or short workspace. */
+wblbe_status wblbe_create(const wblbe_params* params, void* dev_workspace,
+                          size_t workspace_bytes, void* cuda_stream,
+                          wblbe_handle* out);
+
+/* Change tau, kappa, beta, rho_l, rho_g, rho0 or the scheme between steps.
+ * Changing nx, ny, precision or rho_ref returns EINVAL (the stored state
+ * depends on them). */
+wblbe_status wblbe_set_params(wblbe_handle h, const wblbe_params* params);
+
+/* Choose the launch shape (see wblbe_launch).  EINVAL on unsupported
+ * values.  The default is picked from the lattice size at creation. */
+wblbe_status wblbe_set_launch(wblbe_handle h, const wblbe_launch* launch);
+wblbe_status wblbe_get_launch(wblbe_handle h, wblbe_launch* launch);
+
+/* Initial state (Sec. IV): u = 0 and f_i = f_i^eq(rho, u = 0) of the
+ * handle's scheme.  rho: [ny][nx] float64, host or device (rho_on_device).
+ * Resets the step counter and the reference mass. */
+wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho,
+                            int32_t rho_on_device);
+
+/* Advance nsteps >= 0 time steps of Eq. D2Q9 (collision, streaming,
+ * periodic boundaries).  Asynchronous on the handle's stream; repeated
+ * chunks are replayed from a captured CUDA graph. */
+wblbe_status wblbe_step(wblbe_handle h, int64_t nsteps);
+
+/* Step until max|u| < umax_tol, testing every check_every steps (> 0), or
+ * until max_steps further steps were taken.  Blocking.  *steps_done (may be
+ * NULL) receives the steps taken by this call and *out (may be NULL) the
+ * stats of the last check.  Returns OK on convergence, ENOTCONVERGED at
+ * max_steps, EUNSTABLE on a non-finite value. */
+wblbe_status wblbe_run_until_equilibrium(wblbe_handle h, double umax_tol,
+                                         int64_t max_steps,
+                                         int64_t check_every,
+                                         int64_t* steps_done,
+                                         wblbe_stats* out);
+
+/* Macroscopic fields of the current state f(t): rho, u (Eq. rhoU), mu,
+ * as [ny][nx] float64 (each pointer may be NULL), on the host or device
+ * (out_on_device), and the stats (may be NULL).  Synchronises the stream. */
+wblbe_status wblbe_moments(wblbe_handle h, double* rho, double* ux,
+                           double* uy, double* mu, int32_t out_on_device,
+                           wblbe_stats* stats);
+
+/* Copy the populations f_i(x, t) out as [9][ny][nx] float64 (unshifted), or
+ * replace them (which resets the reference mass).  Synchronises. */
+wblbe_status wblbe_get_populations(wblbe_handle h, double* f,
+                                   int32_t on_device);
+wblbe_status wblbe_set_populations(wblbe_handle h, const double* f,
+                                   int32_t on_device);
+
+/* Number of steps taken since the last init, and the number of kernels this
+ * handle has launched (graph replays count every kernel in the graph). */
+int64_t wblbe_step_count(wblbe_handle h);
+int64_t wblbe_kernel_launches(wblbe_handle h);
+
+/* Release the handle (the workspace stays the caller's).  NULL -> EINVAL.
+ * Synchronises the stream first. */
+wblbe_status wblbe_destroy(wblbe_handle h);
+
+/* Last error message of h, or of the calling thread when h is NULL. */
+const char* wblbe_last_error(wblbe_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WBLBE_H */

@@ -1,0 +1,575 @@
+// C-ABI runtime of the well-balanced / standard D2Q9 LBE library
+// (declarations and conventions in include/wblbe.h).
+//
+// A handle owns no device memory: it carves the caller's workspace into two
+// population buffers (ping-pong), one float64 staging field for host I/O,
+// per-CTA reduction partials and a stats record.  Steps are issued on the
+// caller's stream; chunks of steps are captured once into a CUDA graph and
+// replayed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/wblbe.h"
+#include "lbm_kernels.cuh"
+
+using namespace wblbe;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kGraphSteps = 32;          // steps per captured graph (even)
+constexpr int kMomentsRows = 16;         // rows per CTA of the moments kernel
+constexpr int kNumSMs = 152;
+
+thread_local char g_thread_error[256] = "";
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  int pitch;            // elements per row
+  size_t elem;          // bytes per population element
+  long long plane;      // elements per plane
+  size_t pops_bytes;    // one population buffer
+  size_t off_a, off_b, off_stage, off_partials, off_stats, total;
+  int max_partials;
+};
+
+bool params_valid(const wblbe_params* p, char* why, size_t n) {
+  if (!p) { snprintf(why, n, "params is NULL"); return false; }
+  if (p->nx < 1 || p->ny < 1) { snprintf(why, n, "nx, ny must be >= 1"); return false; }
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau)) { snprintf(why, n, "tau must be > 0.5"); return false; }
+  if (!(p->kappa >= 0.0) || !std::isfinite(p->kappa)) { snprintf(why, n, "kappa must be >= 0"); return false; }
+  if (!(p->beta > 0.0) || !std::isfinite(p->beta)) { snprintf(why, n, "beta must be > 0"); return false; }
+  if (!(p->rho_g > 0.0) || !(p->rho_l > p->rho_g) || !std::isfinite(p->rho_l)) {
+    snprintf(why, n, "need rho_l > rho_g > 0"); return false;
+  }
+  if (!std::isfinite(p->rho0)) { snprintf(why, n, "rho0 must be finite"); return false; }
+  if (p->scheme != WBLBE_STANDARD && p->scheme != WBLBE_WELL_BALANCED) {
+    snprintf(why, n, "unknown scheme %d", p->scheme); return false;
+  }
+  if (p->precision != WBLBE_FP64 && p->precision != WBLBE_FP32_SHIFTED) {
+    snprintf(why, n, "unknown precision %d", p->precision); return false;
+  }
+  if (p->precision == WBLBE_FP32_SHIFTED && std::isinf(p->rho_ref)) {
+    snprintf(why, n, "rho_ref must be finite or NaN"); return false;
+  }
+  return true;
+}
+
+Layout make_layout(const wblbe_params* p) {
+  Layout L{};
+  L.elem = p->precision == WBLBE_FP64 ? 8 : 4;
+  const int align_elems = (int)(128 / L.elem);
+  L.pitch = (p->nx + align_elems - 1) / align_elems * align_elems;
+  L.plane = (long long)L.pitch * p->ny;
+  L.pops_bytes = align_up((size_t)9 * (size_t)L.plane * L.elem);
+  const int strips = (p->nx + 31) / 32;
+  const int runs = (p->ny + kMomentsRows - 1) / kMomentsRows;
+  L.max_partials = strips * runs;
+  size_t off = 0;
+  L.off_a = off; off += L.pops_bytes;
+  L.off_b = off; off += L.pops_bytes;
+  L.off_stage = off; off += align_up((size_t)p->nx * p->ny * sizeof(double));
+  L.off_partials = off; off += align_up((size_t)L.max_partials * kStatRec * sizeof(double));
+  L.off_stats = off; off += align_up(8 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct wblbe_ctx {
+  wblbe_params p;
+  Layout L;
+  int device;
+  cudaStream_t stream;
+  cudaStream_t capture_stream;
+  unsigned char* ws;
+  void* buf[2];
+  int cur;                       // buffer holding the state
+  double* stage;
+  double* partials;
+  double* stats_dev;
+  wblbe_launch launch;
+  int64_t steps;
+  int64_t launches;
+  double mass0;
+  bool have_state;
+  cudaGraphExec_t graph;         // kGraphSteps steps starting from buf[0]
+  bool graph_valid;
+  char err[256];
+};
+
+namespace {
+
+wblbe_status fail(wblbe_ctx* h, wblbe_status st, const char* fmt, ...) {
+  char* dst = h ? h->err : g_thread_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(dst, 256, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define CU(h, call)                                                          \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess)                                                   \
+      return fail((h), WBLBE_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Keeps the caller's current device and switches to the handle's.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+double rho_ref_of(const wblbe_params& p) {
+  if (p.precision == WBLBE_FP64) return 0.0;
+  return std::isnan(p.rho_ref) ? 0.5 * (p.rho_l + p.rho_g) : p.rho_ref;
+}
+
+KParams make_kparams(const wblbe_ctx* h, int rows) {
+  const wblbe_params& p = h->p;
+  KParams k{};
+  k.nx = p.nx;
+  k.ny = p.ny;
+  k.pitch = h->L.pitch;
+  k.rows = rows;
+  k.plane = h->L.plane;
+  k.omega = 1.0 / p.tau;
+  k.kforce = 1.0 - 1.0 / (2.0 * p.tau);
+  k.kappa = p.kappa;
+  k.two_beta = 2.0 * p.beta;
+  const double rr = rho_ref_of(p);
+  k.rho_ref = rr;
+  k.dl = rr - p.rho_l;
+  k.dg = rr - p.rho_g;
+  const bool fp64 = p.precision == WBLBE_FP64;
+  const double rho0 = (p.scheme == WBLBE_WELL_BALANCED && fp64) ? p.rho0 : 0.0;
+  k.wb_b0c = (1.0 - 4.0 / 9.0) * rho0;
+  k.wb_bax = rho0 / 9.0;
+  k.wb_bdg = rho0 / 36.0;
+  return k;
+}
+
+LayoutParams make_layout_params(const wblbe_ctx* h) {
+  const wblbe_params& p = h->p;
+  LayoutParams lp{};
+  lp.nx = p.nx;
+  lp.ny = p.ny;
+  lp.pitch = h->L.pitch;
+  lp.plane = h->L.plane;
+  lp.wb = p.scheme == WBLBE_WELL_BALANCED;
+  lp.rho0 = p.rho0;
+  const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+  if (p.precision == WBLBE_FP64) {
+    for (int i = 0; i < 9; ++i) lp.shift[i] = 0.0;
+  } else {
+    const double rr = rho_ref_of(p);
+    for (int i = 0; i < 9; ++i) {
+      if (lp.wb)
+        lp.shift[i] = (i == 0) ? rr - (1.0 - w[0]) * p.rho0 : w[i] * p.rho0;
+      else
+        lp.shift[i] = w[i] * rr;
+    }
+  }
+  return lp;
+}
+
+wblbe_launch default_launch(const wblbe_params& p) {
+  wblbe_launch l{};
+  l.tile_x = p.nx >= 128 ? 128 : (p.nx > 32 ? 64 : 32);
+  const long long strips = (p.nx + l.tile_x - 1) / l.tile_x;
+  const long long target = (long long)kNumSMs * 8;   // about one full wave
+  long long rows = (p.ny * strips + target - 1) / target;
+  if (rows < 4) rows = 4;
+  if (rows > 512) rows = 512;
+  if (rows > p.ny) rows = p.ny;
+  l.rows_per_cta = (int)rows;
+  return l;
+}
+
+bool launch_valid(const wblbe_launch* l) {
+  if (!l) return false;
+  if (l->tile_x != 32 && l->tile_x != 64 && l->tile_x != 128 && l->tile_x != 256) return false;
+  return l->rows_per_cta >= 1;
+}
+
+template <typename T, bool WB, bool MOM>
+cudaError_t launch_strip(const void* src, void* dst, const KParams& kp,
+                         const MomentsOut& mo, int tile, cudaStream_t s) {
+  dim3 grid((kp.nx + tile - 1) / tile, (kp.ny + kp.rows - 1) / kp.rows);
+  size_t smem = 2 * (size_t)kRing * (tile + 2 * kHalo) * sizeof(T);
+  lbm_strip_kernel<T, WB, MOM><<<grid, tile, smem, s>>>(
+      static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
+                       void* dst, const KParams& kp, const MomentsOut& mo,
+                       int tile, cudaStream_t s) {
+  const bool wb = h->p.scheme == WBLBE_WELL_BALANCED;
+  if (h->p.precision == WBLBE_FP64) {
+    if (wb) return moments ? launch_strip<double, true, true>(src, dst, kp, mo, tile, s)
+                           : launch_strip<double, true, false>(src, dst, kp, mo, tile, s);
+    return moments ? launch_strip<double, false, true>(src, dst, kp, mo, tile, s)
+                   : launch_strip<double, false, false>(src, dst, kp, mo, tile, s);
+  }
+  if (wb) return moments ? launch_strip<float, true, true>(src, dst, kp, mo, tile, s)
+                         : launch_strip<float, true, false>(src, dst, kp, mo, tile, s);
+  return moments ? launch_strip<float, false, true>(src, dst, kp, mo, tile, s)
+                 : launch_strip<float, false, false>(src, dst, kp, mo, tile, s);
+}
+
+// One step from buf[from] to buf[1-from] on stream s.
+cudaError_t issue_step(wblbe_ctx* h, int from, cudaStream_t s) {
+  KParams kp = make_kparams(h, h->launch.rows_per_cta);
+  MomentsOut mo{};
+  return launch_any(h, false, h->buf[from], h->buf[1 - from], kp, mo,
+                    h->launch.tile_x, s);
+}
+
+void drop_graph(wblbe_ctx* h) {
+  if (h->graph_valid) cudaGraphExecDestroy(h->graph);
+  h->graph_valid = false;
+}
+
+wblbe_status build_graph(wblbe_ctx* h) {
+  drop_graph(h);
+  cudaGraph_t g = nullptr;
+  CU(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k)
+    le = issue_step(h, k & 1, h->capture_stream);
+  cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(h, WBLBE_ECUDA, "graph capture failed: %s",
+                cudaGetErrorString(le != cudaSuccess ? le : ce));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess)
+    return fail(h, WBLBE_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+  h->graph_valid = true;
+  return WBLBE_OK;
+}
+
+// Moments / stats pass over the current state.  Fields (device pointers, may
+// be null) and the stats record into h->stats_dev.
+wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,
+                         double* mu) {
+  const int tile = h->p.nx >= 128 ? 128 : (h->p.nx > 32 ? 64 : 32);
+  KParams kp = make_kparams(h, kMomentsRows);
+  MomentsOut mo{rho, ux, uy, mu, h->partials};
+  CU(h, launch_any(h, true, h->buf[h->cur], nullptr, kp, mo, tile, h->stream));
+  const int n = ((h->p.nx + tile - 1) / tile) * ((h->p.ny + kMomentsRows - 1) / kMomentsRows);
+  stats_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, n, h->stats_dev);
+  CU(h, cudaGetLastError());
+  h->launches += 2;
+  return WBLBE_OK;
+}
+
+wblbe_status read_stats(wblbe_ctx* h, wblbe_stats* out) {
+  double v[kStatRec];
+  CU(h, cudaMemcpyAsync(v, h->stats_dev, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (out) {
+    out->step = h->steps;
+    out->mass = v[0];
+    out->kinetic = v[1];
+    out->umax = v[2];
+    out->mu_min = v[3];
+    out->mu_max = v[4];
+    out->nonfinite = v[5] != 0.0 || !std::isfinite(v[0]);
+    out->mass_drift_rel = h->mass0 != 0.0 ? (v[0] - h->mass0) / h->mass0 : 0.0;
+  }
+  return WBLBE_OK;
+}
+
+wblbe_status reset_mass(wblbe_ctx* h) {
+  wblbe_status st = run_moments(h, nullptr, nullptr, nullptr, nullptr);
+  if (st != WBLBE_OK) return st;
+  wblbe_stats s{};
+  st = read_stats(h, &s);
+  if (st != WBLBE_OK) return st;
+  h->mass0 = s.mass;
+  return WBLBE_OK;
+}
+
+dim3 layout_grid(const wblbe_ctx* h) {
+  return dim3((h->p.nx + 127) / 128, h->p.ny);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t wblbe_workspace_bytes(const wblbe_params* params) {
+  char why[256];
+  if (!params_valid(params, why, sizeof(why))) return 0;
+  if ((long long)params->ny * ((params->nx + 31) / 32 * 32) >= (1LL << 31)) return 0;
+  return make_layout(params).total;
+}
+
+wblbe_status wblbe_create(const wblbe_params* params, void* dev_workspace,
+                          size_t workspace_bytes, void* cuda_stream,
+                          wblbe_handle* out) {
+  char why[256];
+  if (!out) return fail(nullptr, WBLBE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params_valid(params, why, sizeof(why))) return fail(nullptr, WBLBE_EINVAL, "%s", why);
+  const size_t need = wblbe_workspace_bytes(params);
+  if (need == 0) return fail(nullptr, WBLBE_EINVAL, "lattice too large");
+  if (!dev_workspace || ((uintptr_t)dev_workspace % kAlign) != 0)
+    return fail(nullptr, WBLBE_EINVAL, "workspace must be a 256-byte aligned device pointer");
+  if (workspace_bytes < need)
+    return fail(nullptr, WBLBE_ENOMEM, "workspace has %zu bytes, needs %zu", workspace_bytes, need);
+  wblbe_ctx* h = new (std::nothrow) wblbe_ctx();
+  if (!h) return fail(nullptr, WBLBE_ENOMEM, "host allocation failed");
+  h->p = *params;
+  h->L = make_layout(params);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, WBLBE_ECUDA, "no CUDA device");
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, WBLBE_ECUDA, "cudaStreamCreate failed");
+  }
+  h->ws = static_cast<unsigned char*>(dev_workspace);
+  h->buf[0] = h->ws + h->L.off_a;
+  h->buf[1] = h->ws + h->L.off_b;
+  h->stage = reinterpret_cast<double*>(h->ws + h->L.off_stage);
+  h->partials = reinterpret_cast<double*>(h->ws + h->L.off_partials);
+  h->stats_dev = reinterpret_cast<double*>(h->ws + h->L.off_stats);
+  h->cur = 0;
+  h->launch = default_launch(*params);
+  *out = h;
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_set_params(wblbe_handle h, const wblbe_params* params) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  char why[256];
+  if (!params_valid(params, why, sizeof(why))) return fail(h, WBLBE_EINVAL, "%s", why);
+  if (params->nx != h->p.nx || params->ny != h->p.ny || params->precision != h->p.precision)
+    return fail(h, WBLBE_EINVAL, "nx, ny and precision are fixed for a handle");
+  if (params->precision == WBLBE_FP32_SHIFTED &&
+      (rho_ref_of(*params) != rho_ref_of(h->p) ||
+       (params->scheme != h->p.scheme) || (params->rho0 != h->p.rho0 &&
+                                           params->scheme == WBLBE_WELL_BALANCED)))
+    return fail(h, WBLBE_EINVAL, "the FP32 shift (rho_ref, scheme, rho0) is fixed for a handle");
+  h->p = *params;
+  drop_graph(h);
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_set_launch(wblbe_handle h, const wblbe_launch* launch) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!launch_valid(launch)) return fail(h, WBLBE_EINVAL, "tile_x must be 32/64/128/256 and rows_per_cta >= 1");
+  h->launch = *launch;
+  drop_graph(h);
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_get_launch(wblbe_handle h, wblbe_launch* launch) {
+  if (!h || !launch) return fail(h, WBLBE_EINVAL, "NULL argument");
+  *launch = h->launch;
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho, int32_t rho_on_device) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!rho) return fail(h, WBLBE_EINVAL, "rho is NULL");
+  DeviceGuard dg(h->device);
+  const double* src = rho;
+  if (!rho_on_device) {
+    CU(h, cudaMemcpyAsync(h->stage, rho, (size_t)h->p.nx * h->p.ny * sizeof(double),
+                          cudaMemcpyHostToDevice, h->stream));
+    src = h->stage;
+  }
+  LayoutParams lp = make_layout_params(h);
+  h->cur = 0;
+  if (h->p.precision == WBLBE_FP64)
+    init_rest_kernel<double><<<layout_grid(h), 128, 0, h->stream>>>(src, (double*)h->buf[0], lp);
+  else
+    init_rest_kernel<float><<<layout_grid(h), 128, 0, h->stream>>>(src, (float*)h->buf[0], lp);
+  CU(h, cudaGetLastError());
+  h->launches += 1;
+  h->steps = 0;
+  h->have_state = true;
+  return reset_mass(h);
+}
+
+wblbe_status wblbe_step(wblbe_handle h, int64_t nsteps) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(h, WBLBE_EINVAL, "nsteps must be >= 0");
+  if (!h->have_state) return fail(h, WBLBE_EINVAL, "no state: call wblbe_init_rho first");
+  DeviceGuard dg(h->device);
+  int64_t left = nsteps;
+  if (left >= kGraphSteps) {
+    if (!h->graph_valid) {
+      wblbe_status st = build_graph(h);
+      if (st != WBLBE_OK) return st;
+    }
+    // The graph alternates buf[0] -> buf[1] -> ...; with the state in buf[1]
+    // one direct step first brings it back to buf[0].
+    if (h->cur == 1) {
+      CU(h, issue_step(h, 1, h->stream));
+      h->cur = 0;
+      h->launches += 1;
+      --left;
+    }
+    while (left >= kGraphSteps) {
+      CU(h, cudaGraphLaunch(h->graph, h->stream));
+      h->launches += kGraphSteps;
+      left -= kGraphSteps;
+    }
+  }
+  for (; left > 0; --left) {
+    CU(h, issue_step(h, h->cur, h->stream));
+    h->cur ^= 1;
+    h->launches += 1;
+  }
+  h->steps += nsteps;
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_moments(wblbe_handle h, double* rho, double* ux, double* uy,
+                           double* mu, int32_t out_on_device, wblbe_stats* stats) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!h->have_state) return fail(h, WBLBE_EINVAL, "no state: call wblbe_init_rho first");
+  DeviceGuard dg(h->device);
+  wblbe_status st;
+  if (out_on_device) {
+    st = run_moments(h, rho, ux, uy, mu);
+    if (st != WBLBE_OK) return st;
+  } else {
+    double* outs[4] = {rho, ux, uy, mu};
+    bool any = false;
+    const size_t bytes = (size_t)h->p.nx * h->p.ny * sizeof(double);
+    for (int k = 0; k < 4; ++k) {
+      if (!outs[k]) continue;
+      any = true;
+      double* dev[4] = {nullptr, nullptr, nullptr, nullptr};
+      dev[k] = h->stage;
+      st = run_moments(h, dev[0], dev[1], dev[2], dev[3]);
+      if (st != WBLBE_OK) return st;
+      CU(h, cudaMemcpyAsync(outs[k], h->stage, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (!any) {
+      st = run_moments(h, nullptr, nullptr, nullptr, nullptr);
+      if (st != WBLBE_OK) return st;
+    }
+  }
+  return read_stats(h, stats);
+}
+
+wblbe_status wblbe_run_until_equilibrium(wblbe_handle h, double umax_tol,
+                                         int64_t max_steps, int64_t check_every,
+                                         int64_t* steps_done, wblbe_stats* out) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (check_every < 1 || max_steps < 0 || !(umax_tol >= 0.0))
+    return fail(h, WBLBE_EINVAL, "need check_every >= 1, max_steps >= 0, umax_tol >= 0");
+  if (steps_done) *steps_done = 0;
+  int64_t done = 0;
+  wblbe_stats s{};
+  for (;;) {
+    wblbe_status st = wblbe_moments(h, nullptr, nullptr, nullptr, nullptr, 1, &s);
+    if (st != WBLBE_OK) return st;
+    if (out) *out = s;
+    if (steps_done) *steps_done = done;
+    if (s.nonfinite) return fail(h, WBLBE_EUNSTABLE, "non-finite value at step %lld", (long long)s.step);
+    if (s.umax < umax_tol) return WBLBE_OK;
+    if (done >= max_steps) return fail(h, WBLBE_ENOTCONVERGED, "max|u| = %g after %lld steps", s.umax, (long long)done);
+    int64_t n = check_every < max_steps - done ? check_every : max_steps - done;
+    st = wblbe_step(h, n);
+    if (st != WBLBE_OK) return st;
+    done += n;
+  }
+}
+
+wblbe_status wblbe_get_populations(wblbe_handle h, double* f, int32_t on_device) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!f) return fail(h, WBLBE_EINVAL, "f is NULL");
+  if (!h->have_state) return fail(h, WBLBE_EINVAL, "no state: call wblbe_init_rho first");
+  DeviceGuard dg(h->device);
+  LayoutParams lp = make_layout_params(h);
+  const size_t field = (size_t)h->p.nx * h->p.ny;
+  const bool fp64 = h->p.precision == WBLBE_FP64;
+  if (on_device) {
+    if (fp64) get_pops_kernel<double><<<layout_grid(h), 128, 0, h->stream>>>((const double*)h->buf[h->cur], f, lp, 0, 9);
+    else get_pops_kernel<float><<<layout_grid(h), 128, 0, h->stream>>>((const float*)h->buf[h->cur], f, lp, 0, 9);
+    CU(h, cudaGetLastError());
+    h->launches += 1;
+  } else {
+    for (int i = 0; i < 9; ++i) {
+      if (fp64) get_pops_kernel<double><<<layout_grid(h), 128, 0, h->stream>>>((const double*)h->buf[h->cur], h->stage, lp, i, 1);
+      else get_pops_kernel<float><<<layout_grid(h), 128, 0, h->stream>>>((const float*)h->buf[h->cur], h->stage, lp, i, 1);
+      CU(h, cudaGetLastError());
+      h->launches += 1;
+      CU(h, cudaMemcpyAsync(f + i * field, h->stage, field * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  CU(h, cudaStreamSynchronize(h->stream));
+  return WBLBE_OK;
+}
+
+wblbe_status wblbe_set_populations(wblbe_handle h, const double* f, int32_t on_device) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!f) return fail(h, WBLBE_EINVAL, "f is NULL");
+  DeviceGuard dg(h->device);
+  LayoutParams lp = make_layout_params(h);
+  const size_t field = (size_t)h->p.nx * h->p.ny;
+  const bool fp64 = h->p.precision == WBLBE_FP64;
+  h->cur = 0;
+  if (on_device) {
+    if (fp64) set_pops_kernel<double><<<layout_grid(h), 128, 0, h->stream>>>(f, (double*)h->buf[0], lp, 0, 9);
+    else set_pops_kernel<float><<<layout_grid(h), 128, 0, h->stream>>>(f, (float*)h->buf[0], lp, 0, 9);
+    CU(h, cudaGetLastError());
+    h->launches += 1;
+  } else {
+    for (int i = 0; i < 9; ++i) {
+      CU(h, cudaMemcpyAsync(h->stage, f + i * field, field * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      if (fp64) set_pops_kernel<double><<<layout_grid(h), 128, 0, h->stream>>>(h->stage, (double*)h->buf[0], lp, i, 1);
+      else set_pops_kernel<float><<<layout_grid(h), 128, 0, h->stream>>>(h->stage, (float*)h->buf[0], lp, i, 1);
+      CU(h, cudaGetLastError());
+      h->launches += 1;
+    }
+  }
+  h->have_state = true;
+  h->steps = 0;
+  return reset_mass(h);
+}
+
+int64_t wblbe_step_count(wblbe_handle h) { return h ? h->steps : -1; }
+int64_t wblbe_kernel_launches(wblbe_handle h) { return h ? h->launches : -1; }
+
+wblbe_status wblbe_destroy(wblbe_handle h) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  {
+    DeviceGuard dg(h->device);
+    cudaStreamSynchronize(h->stream);
+    drop_graph(h);
+    cudaStreamDestroy(h->capture_stream);
+  }
+  delete h;
+  return WBLBE_OK;
+}
+
+const char* wblbe_last_error(wblbe_handle h) { return h ? h->err : g_thread_error; }
+
+}  // extern "C"

@@ -1,0 +1,73 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point include/wblbe.h declares; host-only entry points validate arguments."""
+import ctypes
+import math
+import re
+from pathlib import Path
+
+import pytest
+
+from paper_2012_11075_gb300 import wblbe
+
+HEADER = Path(__file__).resolve().parents[1] / "include" / "wblbe.h"
+
+
+def declared_functions():
+    text = re.sub(r"/\*.*?\*/", "", HEADER.read_text(), flags=re.S)
+    return sorted(set(re.findall(r"\b(wblbe_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = declared_functions()
+    for required in ("wblbe_create", "wblbe_set_params", "wblbe_init_rho", "wblbe_step",
+                     "wblbe_run_until_equilibrium", "wblbe_moments", "wblbe_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = wblbe.load_library()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert set(declared_functions()) <= set(wblbe._SIGNATURES)
+
+
+def _params(**kw):
+    base = dict(nx=64, ny=48, tau=0.8, kappa=0.01, beta=0.006, rho_l=1.0, rho_g=0.1)
+    base.update(kw)
+    return wblbe.Params(**base)
+
+
+def test_workspace_bytes_on_host():
+    lib = wblbe.load_library()
+    p64 = _params().c()
+    p32 = _params(precision=wblbe.FP32_SHIFTED).c()
+    b64 = lib.wblbe_workspace_bytes(ctypes.byref(p64))
+    b32 = lib.wblbe_workspace_bytes(ctypes.byref(p32))
+    # two population buffers of 9 planes (rows padded to 128 bytes) at least
+    assert b64 >= 2 * 9 * 48 * 64 * 8
+    assert b32 >= 2 * 9 * 48 * 64 * 4
+    assert b64 % 256 == 0 and b32 % 256 == 0
+    assert b32 < b64
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=-1), dict(tau=0.5), dict(tau=math.nan),
+                                 dict(kappa=-1e-3), dict(beta=0.0), dict(rho_g=0.0),
+                                 dict(rho_l=0.05), dict(scheme=7), dict(precision=3)])
+def test_invalid_parameters_rejected_on_host(bad):
+    lib = wblbe.load_library()
+    p = _params(**bad).c()
+    assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0
+    h = ctypes.c_void_p()
+    st = lib.wblbe_create(ctypes.byref(p), ctypes.c_void_p(256), 1 << 30, None, ctypes.byref(h))
+    assert st == wblbe.EINVAL
+    assert lib.wblbe_last_error(None)
+
+
+def test_null_handle_calls_return_einval():
+    lib = wblbe.load_library()
+    assert lib.wblbe_step(None, 1) == wblbe.EINVAL
+    assert lib.wblbe_destroy(None) == wblbe.EINVAL
+    assert lib.wblbe_init_rho(None, None, 0) == wblbe.EINVAL
+    assert lib.wblbe_moments(None, None, None, None, None, 0, None) == wblbe.EINVAL
+    assert lib.wblbe_step_count(None) == -1

@@ -1,0 +1,244 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances:
+  * FP64 storage: populations within 1e-12 of the oracle, relative to the
+    largest population (global max norm), after 1000 steps.  The two sides
+    differ only in rounding (fused multiply-adds and summation order on the
+    GPU), which stays at round-off level in these stable runs.
+  * FP32-shifted storage: float32 has a unit round-off of 6e-8; an O(1)
+    population accumulates O(steps * 6e-8 * |g|) of rounding in a
+    non-chaotic run, so after 1000 steps we allow 2e-5 of the largest
+    population and 2e-5 absolute on rho, 1e-6 on u.
+  * Different launch shapes and graph replays must give bit-identical
+    populations: the per-node arithmetic does not depend on the tiling.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import STANDARD, WELL_BALANCED
+from paper_2012_11075_gb300 import wblbe
+from paper_2012_11075_gb300 import workloads as wl
+from tests.gpu_helpers import need_gpu, pop_error, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_POP_TOL = 2e-5
+FP32_RHO_TOL = 2e-5
+FP32_U_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+    wblbe.load_library()
+
+
+def _check_fp64(pr, scheme, steps, rho0=0.0, launch=None, rho=None):
+    fg, mg, sg = run_gpu(pr, scheme, steps, launch=launch, rho0=rho0, rho=rho)
+    fo, mo, so = run_oracle(pr, scheme, steps, rho0=rho0, rho=rho)
+    glob, per = pop_error(fg, fo)
+    assert np.all(np.isfinite(fg))
+    assert glob < FP64_TOL, (glob, per)
+    for k in ("rho", "ux", "uy", "mu"):
+        scale = max(np.max(np.abs(mo[k])), 1e-300)
+        assert np.max(np.abs(mg[k] - mo[k])) <= max(FP64_TOL * scale, 1e-15), k
+    assert abs(sg["mass"] - so["mass"]) <= 1e-13 * so["mass"]
+    return glob, per
+
+
+# ---- FP64 against the oracle ---------------------------------------------------
+
+def test_fp64_wb_flat_interface_1000_steps():
+    """Flat interface, 4 x 256 periodic, rho_l = 1, rho_g = 0.1, kappa = 0.01,
+    W = 4, tau = 0.8, well-balanced scheme."""
+    _check_fp64(wl.flat_interface(), WELL_BALANCED, 1000)
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0])
+def test_fp64_wb_droplet_256_1000_steps(tau):
+    """Stationary droplet, 256 x 256, R = 40, W = 4, well-balanced scheme."""
+    _check_fp64(wl.droplet(n=256, radius=40.0, tau=tau), WELL_BALANCED, 1000)
+
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_fp64_paper_flat_interface_both_schemes(scheme):
+    """The 21 x 101 noisy slab of Sec. IV.A (rho_v = 0.2, tau = 0.85)."""
+    _check_fp64(wl.paper_flat(), scheme, 1000)
+
+
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_fp64_paper_droplet_both_schemes(scheme):
+    _check_fp64(wl.paper_droplet(), scheme, 1000)
+
+
+@pytest.mark.parametrize("shape", [(3, 3), (1, 17), (17, 1), (5, 2), (2, 5), (67, 129),
+                                   (64, 80), (257, 33)])
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_fp64_ragged_and_tiny_lattices(shape, scheme):
+    """Lattices narrower than the stencil (the radius-2 halo wraps onto
+    itself), single rows/columns and ragged tails of several tiles."""
+    nx, ny = shape
+    rng = np.random.default_rng(nx * 1000 + ny)
+    rho = 0.6 + 0.3 * rng.uniform(-1, 1, (ny, nx))
+    pr = wl.Problem(nx, ny, 0.85, 0.0128, 0.01, 1.0, 0.2, rho, name=f"rand{nx}x{ny}")
+    _check_fp64(pr, scheme, 100)
+
+
+@pytest.mark.parametrize("rho0", [0.2, 0.55])
+def test_fp64_wb_nonzero_rho0(rho0):
+    pr = wl.droplet(n=64, radius=16.0, tau=0.9, rho_g=0.2)
+    _check_fp64(pr, WELL_BALANCED, 500, rho0=rho0)
+
+
+def test_fp64_full_size_two_steps():
+    """The 4096 x 4096 large-domain case (64 droplets, ratio 10, W = 5,
+    tau = 0.7) in the default launch shape, two steps, full field."""
+    pr = wl.large_domain(n=4096, count=64, ratio=10.0)
+    _check_fp64(pr, WELL_BALANCED, 2)
+
+
+# ---- tiling and graph invariance (bitwise) ---------------------------------------
+
+@pytest.mark.parametrize("precision", [wblbe.FP64, wblbe.FP32_SHIFTED])
+def test_launch_shape_does_not_change_results(precision):
+    pr = wl.droplet(n=200, radius=50.0, tau=0.7, nx=200, ny=150)
+    ref = None
+    for launch in [(32, 1), (64, 7), (128, 16), (256, 512), (128, 150)]:
+        f, _, _ = run_gpu(pr, WELL_BALANCED, 37, precision=precision, launch=launch)
+        if ref is None:
+            ref = f
+        else:
+            assert np.array_equal(f, ref), launch
+
+
+@pytest.mark.parametrize("precision", [wblbe.FP64, wblbe.FP32_SHIFTED])
+def test_graph_replay_equals_single_steps(precision):
+    pr = wl.droplet(n=96, radius=20.0, tau=0.8)
+    from tests.gpu_helpers import gpu_params
+    a = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    b = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    a.init_rho(pr.rho)
+    b.init_rho(pr.rho)
+    a.step(101)                      # 3 graph replays + tail
+    for _ in range(101):
+        b.step(1)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    assert a.steps == b.steps == 101
+    a.close()
+    b.close()
+
+
+# ---- FP32-shifted storage against the FP64 oracle ----------------------------------
+
+@pytest.mark.parametrize("case", ["flat", "droplet"])
+def test_fp32_shifted_against_oracle(case):
+    if case == "flat":
+        pr = wl.flat_interface()
+    else:
+        pr = wl.droplet(n=128, radius=30.0, tau=0.8)
+    steps = 1000
+    fg, mg, sg = run_gpu(pr, WELL_BALANCED, steps, precision=wblbe.FP32_SHIFTED)
+    fo, mo, so = run_oracle(pr, WELL_BALANCED, steps)
+    glob, _ = pop_error(fg, fo)
+    assert glob < FP32_POP_TOL, glob
+    assert np.max(np.abs(mg["rho"] - mo["rho"])) < FP32_RHO_TOL
+    assert np.max(np.abs(mg["ux"] - mo["ux"])) < FP32_U_TOL
+    assert np.max(np.abs(mg["uy"] - mo["uy"])) < FP32_U_TOL
+    assert abs(sg["mass"] - so["mass"]) < 1e-6 * so["mass"]
+
+
+def test_fp32_full_size_two_steps():
+    pr = wl.large_domain(n=4096, count=64, ratio=10.0)
+    fg, mg, _ = run_gpu(pr, WELL_BALANCED, 2, precision=wblbe.FP32_SHIFTED)
+    fo, mo, _ = run_oracle(pr, WELL_BALANCED, 2)
+    glob, _ = pop_error(fg, fo)
+    assert glob < 1e-6, glob
+    assert np.max(np.abs(mg["rho"] - mo["rho"])) < 1e-6
+
+
+# ---- state I/O, stats and errors ----------------------------------------------------
+
+@pytest.mark.parametrize("precision", [wblbe.FP64, wblbe.FP32_SHIFTED])
+def test_population_round_trip_and_device_moments(precision):
+    torch = need_gpu()
+    pr = wl.droplet(n=48, radius=12.0, tau=0.8, nx=48, ny=40)
+    from tests.gpu_helpers import gpu_params
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    s.init_rho(pr.rho)
+    s.step(25)
+    f = s.get_populations()
+    s.set_populations(f)
+    f2 = s.get_populations()
+    if precision == wblbe.FP64:
+        assert np.array_equal(f, f2)
+    else:
+        assert np.max(np.abs(f - f2)) < 1e-7
+    host, st_h = s.moments(device=False)
+    dev, st_d = s.moments(device=True)
+    for k in host:
+        assert np.array_equal(host[k], dev[k].cpu().numpy())
+    assert st_h["mass"] == st_d["mass"]
+    # rho from the device init path equals the host init path
+    s2 = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    s2.init_rho(torch.from_numpy(pr.rho).cuda())
+    s.init_rho(pr.rho)
+    assert np.array_equal(s.get_populations(), s2.get_populations())
+    s.close()
+    s2.close()
+
+
+def test_stats_match_oracle():
+    pr = wl.droplet(n=64, radius=16.0, tau=0.85, rho_g=0.2)
+    _, _, sg = run_gpu(pr, WELL_BALANCED, 300)
+    _, _, so = run_oracle(pr, WELL_BALANCED, 300)
+    assert sg["mass"] == pytest.approx(so["mass"], rel=1e-13)
+    assert sg["umax"] == pytest.approx(so["umax"], rel=1e-9)
+    assert sg["mu_min"] == pytest.approx(so["mu_min"], rel=1e-9, abs=1e-15)
+    assert sg["mu_max"] == pytest.approx(so["mu_max"], rel=1e-9, abs=1e-15)
+    assert sg["kinetic"] == pytest.approx(so["kinetic"], rel=1e-9)
+    assert not sg["nonfinite"]
+    assert abs(sg["mass_drift_rel"]) < 1e-13
+
+
+def test_invalid_calls_and_unstable_state():
+    from tests.gpu_helpers import gpu_params
+    pr = wl.droplet(n=32, radius=8.0)
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED))
+    with pytest.raises(wblbe.WblbeError) as e:
+        s.step(1)                                     # no state yet
+    assert e.value.status == wblbe.EINVAL
+    bad = gpu_params(pr, WELL_BALANCED)
+    bad.nx = 33
+    with pytest.raises(wblbe.WblbeError):
+        s.set_params(bad)
+    with pytest.raises(wblbe.WblbeError):
+        s.set_launch(48, 4)
+    rho = pr.rho.copy()
+    rho[5, 7] = math.nan
+    s.init_rho(rho)
+    code, done, st = s.run_until_equilibrium(1e-12, 100, 10)
+    assert code == wblbe.EUNSTABLE and st["nonfinite"]
+    s.close()
+
+
+def test_run_until_equilibrium_reaches_wb_round_off():
+    """The odd flat slab the oracle pins (1 x 21, tau = 0.8) relaxes on the
+    GPU to max|u| at round-off; the call stops at the first check below the
+    tolerance."""
+    ny = 21
+    y = np.arange(ny, dtype=float)
+    d = np.minimum(y, ny - y)
+    prof = 0.55 + 0.45 * np.tanh(2 * (d - ny / 4) / 4.0)
+    pr = wl.Problem(1, ny, 0.8, 0.01, wl.beta_for_width(0.01, 4.0, 1.0, 0.1), 1.0, 0.1,
+                    prof[:, None].copy())
+    from tests.gpu_helpers import gpu_params
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED))
+    s.init_rho(pr.rho)
+    code, done, st = s.run_until_equilibrium(1e-13, 200000, 1000)
+    assert code == wblbe.OK
+    assert st["umax"] < 1e-13 and done <= 60000
+    assert st["mu_max"] - st["mu_min"] < 1e-12
+    s.close()
