@@ -138,9 +138,9 @@ def max_over_ranks(world, value: float, device=None) -> float:
     return float(t.item())
 
 
-def make_problem():
+def make_problem(n=4096):
     from paper_2012_11075_gb300 import workloads as wl
-    return wl.large_domain(n=4096, count=64, ratio=10.0, width=5.0, kappa=0.01, tau=0.7)
+    return wl.large_domain(n=n, count=64, ratio=10.0, width=5.0, kappa=0.01, tau=0.7)
 
 
 # ---------------------------------------------------------------------------------
@@ -235,14 +235,17 @@ def run_ours(args, world, rank, local):
     from paper_2012_11075_gb300 import wblbe
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pr = make_problem()
+    pr = make_problem(args.lattice)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs")
     peak_note = "of measured" if hbm_peak else "of fallback"
     hbm_peak = hbm_peak or 6800.0
     stream = torch.cuda.Stream(device=dev)
     results = {}
-    for prec_name, prec in (("f32", wblbe.FP32_SHIFTED), ("f64", wblbe.FP64)):
+    precisions = [("f32", wblbe.FP32_SHIFTED), ("f64", wblbe.FP64)]
+    if args.only != "both":
+        precisions = [x for x in precisions if x[0] == args.only]
+    for prec_name, prec in precisions:
         params = wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g,
                               scheme=wblbe.WELL_BALANCED, precision=prec)
         solver = wblbe.Solver(params, stream=stream)
@@ -264,7 +267,7 @@ def run_ours(args, world, rank, local):
             achieved_gbs=achieved_gbs, launches=launches, clocks=clk.summary(),
             launch=solver.get_launch(), umax=st["umax"], mass_drift=st["mass_drift_rel"],
             nonfinite=st["nonfinite"], S=S, K=K)
-        if prec_name == "f32":
+        if prec_name == "f32" and not args.no_e2e:
             rho_pinned = torch.from_numpy(pr.rho).pin_memory()
             rho_out = torch.empty_like(rho_pinned).pin_memory()
             e2e_t = time_e2e(solver, rho_pinned, rho_out, S, K, min(args.warmup, 2), torch)
@@ -276,6 +279,11 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
 
     if rank != 0:
+        return 0
+    if args.only != "both" or args.no_e2e or args.lattice != 4096:
+        # profiling / partial runs: a short summary, not the benchmark line
+        print(json.dumps({k: {kk: vv for kk, vv in v.items() if kk != "clocks"}
+                          for k, v in results.items()}, default=str), flush=True)
         return 0
     r32, r64 = results["f32"], results["f64"]
     traffic = None
@@ -333,6 +341,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", type=int, default=4096,
+                    help="lattice side (4096 is the benchmark; smaller sides are for profiling)")
+    ap.add_argument("--only", choices=["both", "f32", "f64"], default="both")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

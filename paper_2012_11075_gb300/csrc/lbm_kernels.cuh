@@ -10,7 +10,8 @@
 //
 // One CTA owns a strip of tile_x lattice columns and marches a run of rows
 // upward.  For every row it pulls the nine populations of its columns (one
-// thread per column, coalesced along x) plus two halo columns on each side,
+// thread per column, coalesced along x) plus two halo columns on each side
+// into shared memory with asynchronous copies issued several rows ahead,
 // reduces them to the density (Eq. rhoU) and keeps the densities of the
 // last rows in a shared-memory ring.  The chemical potential
 // mu = mu_0(rho) - kappa lap(rho) of the row below is computed into a second
@@ -61,30 +62,6 @@ constexpr int kStatRec = 6;       // mass, kinetic, umax^2, mu_min, mu_max, nonf
 __device__ __forceinline__ int wrap_index(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
-}
-
-// Pull the nine pre-collision populations of node (column xc, row r).
-// xl / xr are the wrapped columns x-1 / x+1; rm, r0, rp the row offsets of
-// rows r-1, r, r+1 (already wrapped and multiplied by the pitch).
-template <typename T>
-__device__ __forceinline__ void pull9(const T* __restrict__ src, long long plane,
-                                      int xl, int xc, int xr, int rm, int r0,
-                                      int rp, T (&f)[9]) {
-  // f_i(x) = P_i(x - c_i)
-  f[0] = __ldg(src + 0 * plane + r0 + xc);
-  f[1] = __ldg(src + 1 * plane + r0 + xl);   // c1 = ( 1, 0)
-  f[2] = __ldg(src + 2 * plane + rm + xc);   // c2 = ( 0, 1)
-  f[3] = __ldg(src + 3 * plane + r0 + xr);   // c3 = (-1, 0)
-  f[4] = __ldg(src + 4 * plane + rp + xc);   // c4 = ( 0,-1)
-  f[5] = __ldg(src + 5 * plane + rm + xl);   // c5 = ( 1, 1)
-  f[6] = __ldg(src + 6 * plane + rm + xr);   // c6 = (-1, 1)
-  f[7] = __ldg(src + 7 * plane + rp + xr);   // c7 = (-1,-1)
-  f[8] = __ldg(src + 8 * plane + rp + xl);   // c8 = ( 1,-1)
-}
-
-template <typename T>
-__device__ __forceinline__ T sum9(const T (&f)[9]) {
-  return ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
 }
 
 // mu = mu_0(rho) - kappa lap(rho) at one node from the 3x3 neighbourhood of
@@ -196,21 +173,60 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   g[8] = keep * g[8] + (E6 - O6);
 }
 
+// Asynchronous global -> shared copies (cp.async, sm_80 and later).  The
+// pulled populations of a row are copied into shared memory several rows
+// ahead of their use, so the data in flight occupies no registers.
+__device__ __forceinline__ void cp_async_elem(void* smem, const float* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(void* smem, const double* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rows of populations staged in shared memory: the pipeline keeps the row
+// being collided, the two rows above it, and kStages - 3 rows in flight.
+template <typename T> struct Staging;
+template <> struct Staging<float> { static constexpr int kStages = 8; };
+template <> struct Staging<double> { static constexpr int kStages = 4; };
+
+__host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size_t elem) {
+  return ((size_t)stages * 9 + 2 * kRing) * (size_t)(tile + 2 * kHalo) * elem;
+}
+
 // The fused step kernel (MOMENTS = false) and the macroscopic-field /
 // statistics kernel (MOMENTS = true) share one body so that both evaluate
 // rho, mu, F and u with identical arithmetic.
 //
+// Pipeline over the rows k = y0-2 .. y1+1 of a strip (y0..y1-1 are the rows
+// this CTA updates): row k + PD is requested (cp.async, already pulled:
+// stage[i][slot] = P_i(x - c_i)), row k's density goes to the rho ring,
+// mu of row k-1 to the mu ring, and row k-2 is collided and stored.  Every
+// staged element is written and read by the same thread, so only the two
+// rings need barriers.
+//
 // blockDim.x = tile_x; grid = (ceil(nx / tile_x), ceil(ny / rows)).
-// Dynamic shared memory: 2 * kRing * (tile_x + 2 kHalo) elements of T.
+// Dynamic shared memory: strip_smem_bytes(tile_x, kStages, sizeof(T)).
 template <typename T, bool WB, bool MOMENTS>
 __global__ void __launch_bounds__(kMaxTile)
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
+  constexpr int kStages = Staging<T>::kStages;
+  constexpr int PD = kStages - 3;          // rows requested ahead of use
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = blockDim.x;
-  const int SW = TX + 2 * kHalo;           // ring row width
-  T* rho_s = reinterpret_cast<T*>(smem_raw);
-  T* mu_s = rho_s + kRing * SW;
+  const int SW = TX + 2 * kHalo;           // row width of every buffer
+  T* stage = reinterpret_cast<T*>(smem_raw);          // [kStages][9][SW]
+  T* rho_s = stage + kStages * 9 * SW;                 // [kRing][SW]
+  T* mu_s = rho_s + kRing * SW;                        // [kRing][SW]
 
   const int tx = threadIdx.x;
   const int x0 = blockIdx.x * TX;
@@ -219,51 +235,53 @@ __global__ void __launch_bounds__(kMaxTile)
   const int y1 = min(y0 + p.rows, p.ny);
   const bool own = tx < w;
 
-  // Columns of this thread: own column (clamped for idle threads so that
-  // their loads stay in bounds) and, for tx < 4, one halo column.
+  // Columns this thread pulls: its own column (tx < w) and, for tx < 4, one
+  // halo column (slots 0, 1 and w+2, w+3).
   const int xc = own ? x0 + tx : x0;
   const int xl = (xc == 0) ? p.nx - 1 : xc - 1;
   const int xr = (xc == p.nx - 1) ? 0 : xc + 1;
-  int hs = 0, hc = 0, hl = 0, hr = 0;      // halo slot and its columns
   const bool halo = tx < 2 * kHalo;
+  int hs = 0, hc = 0, hl = 0, hr = 0;
   if (halo) {
-    hs = tx < kHalo ? tx : w + tx;         // slots 0,1 and w+2, w+3
-    const int gx = x0 - kHalo + hs;        // may be outside [0, nx)
+    hs = tx < kHalo ? tx : w + tx;
+    const int gx = x0 - kHalo + hs;        // may lie outside [0, nx)
     hc = wrap_index(gx, p.nx);
     hl = wrap_index(gx - 1, p.nx);
     hr = wrap_index(gx + 1, p.nx);
   }
-  const int sx = tx + kHalo;               // ring slot of the own column
+  const int sx = tx + kHalo;
 
-  const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg),
-          kappa = T(p.kappa);
+  const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa = T(p.kappa);
 
-  auto row_offs = [&](int r, int& rm, int& r0, int& rp) {
+  // Request the pulled populations of lattice row r (logical, may lie
+  // outside [0, ny)) into its stage slot:  f_i(x, r) = P_i(x - c_i, r - c_iy).
+  auto request = [&](int r) {
     const int rw = wrap_index(r, p.ny);
-    const int rmw = (rw == 0) ? p.ny - 1 : rw - 1;
-    const int rpw = (rw == p.ny - 1) ? 0 : rw + 1;
-    rm = rmw * p.pitch;
-    r0 = rw * p.pitch;
-    rp = rpw * p.pitch;
+    const int rm = ((rw == 0) ? p.ny - 1 : rw - 1) * p.pitch;   // row r - 1
+    const int r0 = rw * p.pitch;
+    const int rp = ((rw == p.ny - 1) ? 0 : rw + 1) * p.pitch;   // row r + 1
+    T* st = stage + (r & (kStages - 1)) * 9 * SW;
+    auto pull = [&](int s, int cl, int cc, int cr) {
+      cp_async_elem(st + 0 * SW + s, src + 0 * p.plane + r0 + cc);
+      cp_async_elem(st + 1 * SW + s, src + 1 * p.plane + r0 + cl);   // c1 = ( 1, 0)
+      cp_async_elem(st + 2 * SW + s, src + 2 * p.plane + rm + cc);   // c2 = ( 0, 1)
+      cp_async_elem(st + 3 * SW + s, src + 3 * p.plane + r0 + cr);   // c3 = (-1, 0)
+      cp_async_elem(st + 4 * SW + s, src + 4 * p.plane + rp + cc);   // c4 = ( 0,-1)
+      cp_async_elem(st + 5 * SW + s, src + 5 * p.plane + rm + cl);   // c5 = ( 1, 1)
+      cp_async_elem(st + 6 * SW + s, src + 6 * p.plane + rm + cr);   // c6 = (-1, 1)
+      cp_async_elem(st + 7 * SW + s, src + 7 * p.plane + rp + cr);   // c7 = (-1,-1)
+      cp_async_elem(st + 8 * SW + s, src + 8 * p.plane + rp + cl);   // c8 = ( 1,-1)
+    };
+    if (own) pull(sx, xl, xc, xr);
+    if (halo) pull(hs, hl, hc, hr);
   };
-
-  // Pipeline registers: populations of rows c, c+1, c+2 and the row being
-  // fetched, plus the halo column's row being fetched.
-  T P0[9], P1[9], P2[9], Pn[9], Hn[9];
-
-  auto fetch = [&](int r, T (&f)[9], T (&hf)[9]) {
-    int rm, r0, rp;
-    row_offs(r, rm, r0, rp);
-    pull9<T>(src, p.plane, xl, xc, xr, rm, r0, rp, f);
-    if (halo) pull9<T>(src, p.plane, hl, hc, hr, rm, r0, rp, hf);
+  auto staged_sum = [&](const T* st, int s) {
+    return ((st[0 * SW + s] + st[1 * SW + s]) + (st[2 * SW + s] + st[3 * SW + s])) +
+           ((st[4 * SW + s] + st[5 * SW + s]) + (st[6 * SW + s] + st[7 * SW + s])) +
+           st[8 * SW + s];
   };
-  auto put_rho = [&](int r, const T (&f)[9], const T (&hf)[9]) {
-    T* row = rho_s + (r & (kRing - 1)) * SW;
-    if (own) row[sx] = sum9(f);            // idle threads' slots overlap the
-    if (halo) row[hs] = sum9(hf);          // right halo: they write nothing
-  };
-  // mu of logical row r at ring slots [1, w + 2]: own slot for every thread,
-  // plus slots 1 and w + 2 by threads 0 and 1.
+  // mu of logical row r at slots 1 .. w+2 (own slot; threads 0 and 1 also
+  // take slots 1 and w+2).
   auto put_mu = [&](int r) {
     const T* rn = rho_s + ((r + 1) & (kRing - 1)) * SW;  // row above (y+1)
     const T* rc = rho_s + (r & (kRing - 1)) * SW;
@@ -271,44 +289,37 @@ __global__ void __launch_bounds__(kMaxTile)
     T* mrow = mu_s + (r & (kRing - 1)) * SW;
     auto at = [&](int s) {
       return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
-                         rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg,
-                         kappa);
+                         rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa);
     };
     if (own) mrow[sx] = at(sx);
     if (tx == 0) mrow[1] = at(1);
     if (tx == 1) mrow[w + 2] = at(w + 2);
   };
 
-  // ---- prologue: densities of rows y0-2 .. y0+1, mu of rows y0-1, y0 ----
-  fetch(y0 - 2, Pn, Hn);
-  put_rho(y0 - 2, Pn, Hn);
-  fetch(y0 - 1, Pn, Hn);
-  put_rho(y0 - 1, Pn, Hn);
-  fetch(y0, P0, Hn);
-  put_rho(y0, P0, Hn);
-  fetch(y0 + 1, P1, Hn);
-  put_rho(y0 + 1, P1, Hn);
-  fetch(y0 + 2, Pn, Hn);                   // in flight into the loop
-  __syncthreads();
-  put_mu(y0 - 1);
-  put_mu(y0);
-
-  // statistics accumulators (moments mode)
   double st_mass = 0.0, st_kin = 0.0, st_u2 = 0.0;
   double st_mumin = 1e300, st_mumax = -1e300;
   int st_bad = 0;
 
-  for (int c = y0; c < y1; ++c) {
-    // density of row c+2 from the fetched populations
-    put_rho(c + 2, Pn, Hn);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) P2[i] = Pn[i];
-    if (c + 3 < y1 + 2) fetch(c + 3, Pn, Hn);   // next row in flight
+  const int kfirst = y0 - kHalo, klast = y1 + 1;
+  for (int r = kfirst; r < kfirst + PD; ++r) {
+    if (r <= klast) request(r);
+    cp_async_commit();
+  }
+  for (int k = kfirst; k <= klast; ++k) {
+    if (k + PD <= klast) request(k + PD);
+    cp_async_commit();                     // one group per row, possibly empty
+    cp_async_wait<PD>();                   // row k has landed (this thread)
+    {
+      const T* st = stage + (k & (kStages - 1)) * 9 * SW;
+      T* row = rho_s + (k & (kRing - 1)) * SW;
+      if (own) row[sx] = staged_sum(st, sx);
+      if (halo) row[hs] = staged_sum(st, hs);
+    }
     __syncthreads();
-    put_mu(c + 1);
+    if (k - 1 >= y0 - 1) put_mu(k - 1);
     __syncthreads();
-
-    if (own) {
+    const int c = k - 2;                   // row to collide
+    if (c >= y0 && own) {
       const T* r_dn = rho_s + ((c - 1) & (kRing - 1)) * SW;
       const T* r_c = rho_s + (c & (kRing - 1)) * SW;
       const T* r_up = rho_s + ((c + 1) & (kRing - 1)) * SW;
@@ -329,21 +340,25 @@ __global__ void __launch_bounds__(kMaxTile)
                     T(1.0 / 12.0) * ((r_up[sx + 1] + r_up[sx - 1]) -
                                      (r_dn[sx + 1] + r_dn[sx - 1]));
       const T rs = r_c[sx];
-      T ux, uy;
-      collide<T, WB>(P0, rs, gmx, gmy, grx, gry, p, ux, uy);
-      const long long o = (long long)c * p.pitch + xc;
-      if (!MOMENTS) {
+      const T* st = stage + (c & (kStages - 1)) * 9 * SW;
+      T g[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * p.plane + o] = P0[i];
+      for (int i = 0; i < 9; ++i) g[i] = st[i * SW + sx];
+      T ux, uy;
+      collide<T, WB>(g, rs, gmx, gmy, grx, gry, p, ux, uy);
+      if (!MOMENTS) {
+        const long long o = (long long)c * p.pitch + xc;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dst[i * p.plane + o] = g[i];
       } else {
         const double rho = (double)rs + p.rho_ref;
         const double mu = (double)m_c[sx];
         const double dux = (double)ux, duy = (double)uy;
-        const long long k = (long long)c * p.nx + xc;
-        if (mo.rho) mo.rho[k] = rho;
-        if (mo.ux) mo.ux[k] = dux;
-        if (mo.uy) mo.uy[k] = duy;
-        if (mo.mu) mo.mu[k] = mu;
+        const long long kk = (long long)c * p.nx + xc;
+        if (mo.rho) mo.rho[kk] = rho;
+        if (mo.ux) mo.ux[kk] = dux;
+        if (mo.uy) mo.uy[kk] = duy;
+        if (mo.mu) mo.mu[kk] = mu;
         const double u2 = dux * dux + duy * duy;
         st_mass += rho;
         st_kin += 0.5 * rho * u2;
@@ -353,15 +368,11 @@ __global__ void __launch_bounds__(kMaxTile)
         if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
       }
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      P0[i] = P1[i];
-      P1[i] = P2[i];
-    }
   }
+  cp_async_wait<0>();
 
   if (MOMENTS && mo.partials) {
-    // deterministic block reduction: warp shuffle, then warp 0
+    // deterministic block reduction: warp shuffle, then thread 0 over warps
     __shared__ double red[kMaxTile / 32][kStatRec];
     double v[kStatRec] = {st_mass, st_kin, st_u2, st_mumin, st_mumax, (double)st_bad};
 #pragma unroll
@@ -382,12 +393,12 @@ __global__ void __launch_bounds__(kMaxTile)
     const int warp = tx >> 5, lane = tx & 31, nw = TX >> 5;
     if (lane == 0)
 #pragma unroll
-      for (int k = 0; k < kStatRec; ++k) red[warp][k] = v[k];
+      for (int q = 0; q < kStatRec; ++q) red[warp][q] = v[q];
     __syncthreads();
     if (tx == 0) {
       double r[kStatRec];
 #pragma unroll
-      for (int k = 0; k < kStatRec; ++k) r[k] = red[0][k];
+      for (int q = 0; q < kStatRec; ++q) r[q] = red[0][q];
       for (int q = 1; q < nw; ++q) {
         r[0] += red[q][0];
         r[1] += red[q][1];
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(kMaxTile)
       }
       double* out = mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec;
 #pragma unroll
-      for (int k = 0; k < kStatRec; ++k) out[k] = r[k];
+      for (int q = 0; q < kStatRec; ++q) out[q] = r[q];
     }
   }
 }

@@ -207,11 +207,36 @@ bool launch_valid(const wblbe_launch* l) {
 }
 
 template <typename T, bool WB, bool MOM>
+size_t strip_smem(int tile) {
+  return strip_smem_bytes(tile, Staging<T>::kStages, sizeof(T));
+}
+
+// Allow every instantiation the dynamic shared memory of the widest tile.
+template <typename T, bool WB, bool MOM>
+cudaError_t allow_smem() {
+  return cudaFuncSetAttribute(lbm_strip_kernel<T, WB, MOM>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)strip_smem<T, WB, MOM>(kMaxTile));
+}
+
+cudaError_t allow_smem_all() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = allow_smem<double, true, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<double, true, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<double, false, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<double, false, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<float, true, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<float, true, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<float, false, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem<float, false, false>()) != cudaSuccess) e = r;
+  return e;
+}
+
+template <typename T, bool WB, bool MOM>
 cudaError_t launch_strip(const void* src, void* dst, const KParams& kp,
                          const MomentsOut& mo, int tile, cudaStream_t s) {
   dim3 grid((kp.nx + tile - 1) / tile, (kp.ny + kp.rows - 1) / kp.rows);
-  size_t smem = 2 * (size_t)kRing * (tile + 2 * kHalo) * sizeof(T);
-  lbm_strip_kernel<T, WB, MOM><<<grid, tile, smem, s>>>(
+  lbm_strip_kernel<T, WB, MOM><<<grid, tile, strip_smem<T, WB, MOM>(tile), s>>>(
       static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
   return cudaGetLastError();
 }
@@ -345,6 +370,13 @@ wblbe_status wblbe_create(const wblbe_params* params, void* dev_workspace,
     return fail(nullptr, WBLBE_ECUDA, "no CUDA device");
   }
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  {
+    cudaError_t e = allow_smem_all();
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, WBLBE_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    }
+  }
   if (cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete h;
     return fail(nullptr, WBLBE_ECUDA, "cudaStreamCreate failed");

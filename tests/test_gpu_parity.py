@@ -42,9 +42,13 @@ def _check_fp64(pr, scheme, steps, rho0=0.0, launch=None, rho=None):
     glob, per = pop_error(fg, fo)
     assert np.all(np.isfinite(fg))
     assert glob < FP64_TOL, (glob, per)
-    for k in ("rho", "ux", "uy", "mu"):
+    for k in ("rho", "ux", "uy"):
         scale = max(np.max(np.abs(mo[k])), 1e-300)
         assert np.max(np.abs(mg[k] - mo[k])) <= max(FP64_TOL * scale, 1e-15), k
+    # mu is a difference of terms of size 2 beta (rho_l - rho_g)^3 that cancel
+    # near equilibrium: its rounding scales with those terms, not with |mu|
+    mu_scale = 2 * pr.beta * (pr.rho_l - pr.rho_g) ** 3
+    assert np.max(np.abs(mg["mu"] - mo["mu"])) <= FP64_TOL * mu_scale
     assert abs(sg["mass"] - so["mass"]) <= 1e-13 * so["mass"]
     return glob, per
 
@@ -57,10 +61,26 @@ def test_fp64_wb_flat_interface_1000_steps():
     _check_fp64(wl.flat_interface(), WELL_BALANCED, 1000)
 
 
-@pytest.mark.parametrize("tau", [0.6, 1.0])
-def test_fp64_wb_droplet_256_1000_steps(tau):
-    """Stationary droplet, 256 x 256, R = 40, W = 4, well-balanced scheme."""
-    _check_fp64(wl.droplet(n=256, radius=40.0, tau=tau), WELL_BALANCED, 1000)
+@pytest.mark.parametrize("tau,steps", [(0.6, 400), (1.0, 1000)])
+def test_fp64_wb_droplet_256(tau, steps):
+    """Stationary droplet, 256 x 256, R = 40, W = 4, well-balanced scheme.
+    At tau = 0.6 the scheme is unstable on this case (the oracle too goes
+    non-finite before step 1000), so parity is taken at step 400."""
+    _check_fp64(wl.droplet(n=256, radius=40.0, tau=tau), WELL_BALANCED, steps)
+
+
+def test_instability_detected_on_both_sides():
+    """tau = 0.6 droplet: both the oracle and the GPU reach non-finite values
+    by step 1000, and run_until_equilibrium reports EUNSTABLE."""
+    pr = wl.droplet(n=256, radius=40.0, tau=0.6)
+    _, _, so = run_oracle(pr, WELL_BALANCED, 1000)
+    assert so["nonfinite"]
+    from tests.gpu_helpers import gpu_params
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED))
+    s.init_rho(pr.rho)
+    code, done, st = s.run_until_equilibrium(1e-12, 1000, 100)
+    assert code == wblbe.EUNSTABLE and st["nonfinite"] and done <= 1000
+    s.close()
 
 
 @pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
@@ -147,7 +167,9 @@ def test_fp32_shifted_against_oracle(case):
     assert np.max(np.abs(mg["rho"] - mo["rho"])) < FP32_RHO_TOL
     assert np.max(np.abs(mg["ux"] - mo["ux"])) < FP32_U_TOL
     assert np.max(np.abs(mg["uy"] - mo["uy"])) < FP32_U_TOL
-    assert abs(sg["mass"] - so["mass"]) < 1e-6 * so["mass"]
+    # float32 rounding of every stored population each step: the relative
+    # mass drift after 1000 steps stays within 1000 * 2^-24 * |g|/rho ~ 1e-5
+    assert abs(sg["mass"] - so["mass"]) < 1e-5 * so["mass"]
 
 
 def test_fp32_full_size_two_steps():
@@ -225,20 +247,25 @@ def test_invalid_calls_and_unstable_state():
 
 
 def test_run_until_equilibrium_reaches_wb_round_off():
-    """The odd flat slab the oracle pins (1 x 21, tau = 0.8) relaxes on the
-    GPU to max|u| at round-off; the call stops at the first check below the
-    tolerance."""
+    """The odd flat slab the oracle pins (1 x 21, tau = 0.8): on the GPU the
+    call stops at the first check with max|u| below 1e-13, and after 50000
+    steps the state is the Newton solution of the discrete equilibrium."""
+    from oracle import equilibrium as eq
     ny = 21
     y = np.arange(ny, dtype=float)
     d = np.minimum(y, ny - y)
     prof = 0.55 + 0.45 * np.tanh(2 * (d - ny / 4) / 4.0)
-    pr = wl.Problem(1, ny, 0.8, 0.01, wl.beta_for_width(0.01, 4.0, 1.0, 0.1), 1.0, 0.1,
-                    prof[:, None].copy())
+    beta = wl.beta_for_width(0.01, 4.0, 1.0, 0.1)
+    pr = wl.Problem(1, ny, 0.8, 0.01, beta, 1.0, 0.1, prof[:, None].copy())
     from tests.gpu_helpers import gpu_params
     s = wblbe.Solver(gpu_params(pr, WELL_BALANCED))
     s.init_rho(pr.rho)
     code, done, st = s.run_until_equilibrium(1e-13, 200000, 1000)
     assert code == wblbe.OK
-    assert st["umax"] < 1e-13 and done <= 60000
-    assert st["mu_max"] - st["mu_min"] < 1e-12
+    assert st["umax"] < 1e-13 and done <= 60000 and done % 1000 == 0
+    s.step(50000 - done)
+    m, st = s.moments()
+    rN, mu_bar = eq.discrete_flat_equilibrium(prof, 0.01, beta, 1.0, 0.1)
+    assert st["mu_max"] - st["mu_min"] < 1e-13
+    assert np.max(np.abs(m["rho"][:, 0] - rN)) < 1e-10
     s.close()
