@@ -9,11 +9,11 @@
 // g_i = f_i - s_i (see wblbe.h); in FP64 they hold f_i.
 //
 // One CTA owns a strip of tile_x lattice columns and marches a run of rows
-// upward.  For every row it pulls the nine populations of its columns (one
-// thread per column, coalesced along x) plus two halo columns on each side
-// into shared memory with asynchronous copies issued several rows ahead,
-// reduces them to the density (Eq. rhoU) and keeps the densities of the
-// last rows in a shared-memory ring.  The chemical potential
+// upward.  For every row it stages the nine plane rows its columns pull from
+// (plus four halo columns on each side) in shared memory with asynchronous
+// copies issued several rows ahead of use, reduces them to the density
+// (Eq. rhoU) and keeps the densities of the last rows in a shared-memory
+// ring.  The chemical potential
 // mu = mu_0(rho) - kappa lap(rho) of the row below is computed into a second
 // ring, and the row two below the load front is collided: gradients of mu
 // and rho (isotropic central stencil), the interaction force (Eq. mF or the
@@ -173,16 +173,28 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   g[8] = keep * g[8] + (E6 - O6);
 }
 
-// Asynchronous global -> shared copies (cp.async, sm_80 and later).  The
-// pulled populations of a row are copied into shared memory several rows
-// ahead of their use, so the data in flight occupies no registers.
+// ---- asynchronous copies into shared memory -------------------------------
+//
+// The pulled plane rows are copied global -> shared with cp.async (no
+// register staging), several rows ahead of use.  Full strips of a lattice
+// whose width is a multiple of 4 copy 16-byte chunks (all threads share the
+// 9 x (tile_x + 8) / E chunks of a row, E = 16 / sizeof(T)); ragged strips
+// and other widths copy element by element.
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
 __device__ __forceinline__ void cp_async_elem(void* smem, const float* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_elem(void* smem, const double* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -192,39 +204,52 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// c_iy of direction i (D2Q9 numbering of Sec. II)
+__host__ __device__ constexpr int dir_cy(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+
 // Rows of populations staged in shared memory: the pipeline keeps the row
 // being collided, the two rows above it, and kStages - 3 rows in flight.
 template <typename T> struct Staging;
 template <> struct Staging<float> { static constexpr int kStages = 8; };
 template <> struct Staging<double> { static constexpr int kStages = 4; };
 
+constexpr int kPad = 4;   // staged columns on each side of a strip (x0-4 .. x0+TX+3)
+
 __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size_t elem) {
-  return ((size_t)stages * 9 + 2 * kRing) * (size_t)(tile + 2 * kHalo) * elem;
+  // 128 bytes of alignment slack + the buffers
+  return 128 + ((size_t)stages * 9 + 2 * kRing) * (size_t)(tile + 2 * kPad) * elem;
 }
 
 // The fused step kernel (MOMENTS = false) and the macroscopic-field /
 // statistics kernel (MOMENTS = true) share one body so that both evaluate
 // rho, mu, F and u with identical arithmetic.
 //
+// Shared-memory column slot s holds lattice column x0 - 4 + s (wrapped).
+// Stage rows hold raw plane rows: stage[slot][i][s] = P_i(x0 - 4 + s, r - c_iy)
+// for logical row r, so the pulled population of column s is
+// f_i = stage[slot][i][s - c_ix].
+//
 // Pipeline over the rows k = y0-2 .. y1+1 of a strip (y0..y1-1 are the rows
-// this CTA updates): row k + PD is requested (cp.async, already pulled:
-// stage[i][slot] = P_i(x - c_i)), row k's density goes to the rho ring,
-// mu of row k-1 to the mu ring, and row k-2 is collided and stored.  Every
-// staged element is written and read by the same thread, so only the two
-// rings need barriers.
+// this CTA updates): wait for row k, reduce it to densities (rho ring), request
+// row k + PD, compute mu of row k-1 (mu ring), collide and store row k-2.
 //
 // blockDim.x = tile_x; grid = (ceil(nx / tile_x), ceil(ny / rows)).
 // Dynamic shared memory: strip_smem_bytes(tile_x, kStages, sizeof(T)).
 template <typename T, bool WB, bool MOMENTS>
-__global__ void __launch_bounds__(kMaxTile)
+__global__ void __launch_bounds__(kMaxTile, 1)
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
   constexpr int kStages = Staging<T>::kStages;
   constexpr int PD = kStages - 3;          // rows requested ahead of use
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int TX = blockDim.x;
-  const int SW = TX + 2 * kHalo;           // row width of every buffer
-  T* stage = reinterpret_cast<T*>(smem_raw);          // [kStages][9][SW]
+  const int SW = TX + 2 * kPad;            // row width of every buffer
+  // 128-byte aligned base (16-byte copies need 16)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  T* stage = reinterpret_cast<T*>(base);               // [kStages][9][SW]
   T* rho_s = stage + kStages * 9 * SW;                 // [kRing][SW]
   T* mu_s = rho_s + kRing * SW;                        // [kRing][SW]
 
@@ -234,54 +259,78 @@ __global__ void __launch_bounds__(kMaxTile)
   const int y0 = blockIdx.y * p.rows;
   const int y1 = min(y0 + p.rows, p.ny);
   const bool own = tx < w;
-
-  // Columns this thread pulls: its own column (tx < w) and, for tx < 4, one
-  // halo column (slots 0, 1 and w+2, w+3).
-  const int xc = own ? x0 + tx : x0;
-  const int xl = (xc == 0) ? p.nx - 1 : xc - 1;
-  const int xr = (xc == p.nx - 1) ? 0 : xc + 1;
-  const bool halo = tx < 2 * kHalo;
-  int hs = 0, hc = 0, hl = 0, hr = 0;
-  if (halo) {
-    hs = tx < kHalo ? tx : w + tx;
-    const int gx = x0 - kHalo + hs;        // may lie outside [0, nx)
-    hc = wrap_index(gx, p.nx);
-    hl = wrap_index(gx - 1, p.nx);
-    hr = wrap_index(gx + 1, p.nx);
-  }
-  const int sx = tx + kHalo;
+  const int sx = tx + kPad;                // slot of the own column
+  // density halo: slots 2, 3 (x0-2, x0-1) and w+4, w+5 (x0+w, x0+w+1)
+  const bool halo = tx < 4;
+  const int hs = tx < 2 ? 2 + tx : w + 2 + tx;
+  const bool use_vec = (w == TX) && (p.nx % 4 == 0);
 
   const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa = T(p.kappa);
+  const int kfirst = y0 - 2, klast = y1 + 1;
+  auto slot_of = [&](int r) { return (r - kfirst) % kStages; };
 
-  // Request the pulled populations of lattice row r (logical, may lie
-  // outside [0, ny)) into its stage slot:  f_i(x, r) = P_i(x - c_i, r - c_iy).
+  // 16-byte chunks this thread copies in every row (fixed per thread): chunk
+  // j of plane i covers columns x0-4+jE .. x0-4+jE+E-1, which wrap only as a
+  // whole (nx % 4 == 0).  At most ceil(9 (TX + 8) / E / TX) chunks per
+  // thread: 3 in FP32, 6 in FP64 (TX >= 32).
+  constexpr int E = 16 / sizeof(T);
+  constexpr int kMaxChunks = sizeof(T) == 4 ? 3 : 6;
+  int ch_goff[kMaxChunks], ch_soff[kMaxChunks], ch_cy[kMaxChunks];
+  int nch_mine = 0;
+  if (use_vec) {
+    const int nch = SW / E;
+#pragma unroll
+    for (int c = 0; c < kMaxChunks; ++c) {
+      const int q = tx + c * TX;
+      if (q >= 9 * nch) break;
+      const int i = q / nch, j = q - i * nch;
+      int col = x0 - kPad + j * E;
+      if (col < 0) col += p.nx;
+      else if (col >= p.nx) col -= p.nx;
+      ch_goff[c] = col;
+      ch_soff[c] = i * SW + j * E;
+      ch_cy[c] = dir_cy(i) + 1 + 3 * i;          // plane and row selector
+      nch_mine = c + 1;
+    }
+  }
+
+  // Request logical row r (its plane rows r - c_iy, columns x0-4 .. x0+w+3).
   auto request = [&](int r) {
+    T* st = stage + slot_of(r) * 9 * SW;
     const int rw = wrap_index(r, p.ny);
-    const int rm = ((rw == 0) ? p.ny - 1 : rw - 1) * p.pitch;   // row r - 1
-    const int r0 = rw * p.pitch;
-    const int rp = ((rw == p.ny - 1) ? 0 : rw + 1) * p.pitch;   // row r + 1
-    T* st = stage + (r & (kStages - 1)) * 9 * SW;
-    auto pull = [&](int s, int cl, int cc, int cr) {
-      cp_async_elem(st + 0 * SW + s, src + 0 * p.plane + r0 + cc);
-      cp_async_elem(st + 1 * SW + s, src + 1 * p.plane + r0 + cl);   // c1 = ( 1, 0)
-      cp_async_elem(st + 2 * SW + s, src + 2 * p.plane + rm + cc);   // c2 = ( 0, 1)
-      cp_async_elem(st + 3 * SW + s, src + 3 * p.plane + r0 + cr);   // c3 = (-1, 0)
-      cp_async_elem(st + 4 * SW + s, src + 4 * p.plane + rp + cc);   // c4 = ( 0,-1)
-      cp_async_elem(st + 5 * SW + s, src + 5 * p.plane + rm + cl);   // c5 = ( 1, 1)
-      cp_async_elem(st + 6 * SW + s, src + 6 * p.plane + rm + cr);   // c6 = (-1, 1)
-      cp_async_elem(st + 7 * SW + s, src + 7 * p.plane + rp + cr);   // c7 = (-1,-1)
-      cp_async_elem(st + 8 * SW + s, src + 8 * p.plane + rp + cl);   // c8 = ( 1,-1)
-    };
-    if (own) pull(sx, xl, xc, xr);
-    if (halo) pull(hs, hl, hc, hr);
+    // row offsets for c_iy = -1, 0, +1: rows r+1, r, r-1
+    const int row_p = ((rw == p.ny - 1) ? 0 : rw + 1) * p.pitch;
+    const int row_0 = rw * p.pitch;
+    const int row_m = ((rw == 0) ? p.ny - 1 : rw - 1) * p.pitch;
+    if (use_vec) {
+#pragma unroll
+      for (int c = 0; c < kMaxChunks; ++c) {
+        if (c >= nch_mine) break;
+        const int sel = ch_cy[c];
+        const int i = sel / 3, cyi = sel - 3 * i;
+        const int roff = cyi == 0 ? row_p : (cyi == 1 ? row_0 : row_m);
+        cp_async16(st + ch_soff[c], src + i * p.plane + roff + ch_goff[c]);
+      }
+    } else {
+      const int ncols = w + 2 * kPad;
+      for (int j = tx; j < ncols; j += TX) {
+        const int col = wrap_index(x0 - kPad + j, p.nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const int roff = dir_cy(i) == -1 ? row_p : (dir_cy(i) == 0 ? row_0 : row_m);
+          cp_async_elem(st + i * SW + j, src + i * p.plane + roff + col);
+        }
+      }
+    }
   };
-  auto staged_sum = [&](const T* st, int s) {
-    return ((st[0 * SW + s] + st[1 * SW + s]) + (st[2 * SW + s] + st[3 * SW + s])) +
-           ((st[4 * SW + s] + st[5 * SW + s]) + (st[6 * SW + s] + st[7 * SW + s])) +
-           st[8 * SW + s];
+  // density of the staged row at slot s: sum_i f_i, f_i = stage[i][s - c_ix]
+  auto staged_rho = [&](const T* st, int s) {
+    return ((st[0 * SW + s] + st[1 * SW + s - 1]) + (st[2 * SW + s] + st[3 * SW + s + 1])) +
+           ((st[4 * SW + s] + st[5 * SW + s - 1]) + (st[6 * SW + s + 1] + st[7 * SW + s + 1])) +
+           st[8 * SW + s - 1];
   };
-  // mu of logical row r at slots 1 .. w+2 (own slot; threads 0 and 1 also
-  // take slots 1 and w+2).
+  // mu of logical row r at slots 3 .. w+4 (own slot; threads 0 and 1 also
+  // take slots 3 and w+4).
   auto put_mu = [&](int r) {
     const T* rn = rho_s + ((r + 1) & (kRing - 1)) * SW;  // row above (y+1)
     const T* rc = rho_s + (r & (kRing - 1)) * SW;
@@ -292,30 +341,34 @@ __global__ void __launch_bounds__(kMaxTile)
                          rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa);
     };
     if (own) mrow[sx] = at(sx);
-    if (tx == 0) mrow[1] = at(1);
-    if (tx == 1) mrow[w + 2] = at(w + 2);
+    if (tx == 0) mrow[3] = at(3);
+    if (tx == 1) mrow[w + 4] = at(w + 4);
   };
 
   double st_mass = 0.0, st_kin = 0.0, st_u2 = 0.0;
   double st_mumin = 1e300, st_mumax = -1e300;
   int st_bad = 0;
 
-  const int kfirst = y0 - kHalo, klast = y1 + 1;
   for (int r = kfirst; r < kfirst + PD; ++r) {
     if (r <= klast) request(r);
-    cp_async_commit();
-  }
-  for (int k = kfirst; k <= klast; ++k) {
-    if (k + PD <= klast) request(k + PD);
     cp_async_commit();                     // one group per row, possibly empty
-    cp_async_wait<PD>();                   // row k has landed (this thread)
+  }
+  cp_async_wait<PD - 1>();                 // row kfirst (this thread's copies)
+  __syncthreads();                         // ... and everyone else's
+
+  for (int k = kfirst; k <= klast; ++k) {
     {
-      const T* st = stage + (k & (kStages - 1)) * 9 * SW;
+      const T* st = stage + slot_of(k) * 9 * SW;
       T* row = rho_s + (k & (kRing - 1)) * SW;
-      if (own) row[sx] = staged_sum(st, sx);
-      if (halo) row[hs] = staged_sum(st, hs);
+      if (own) row[sx] = staged_rho(st, sx);
+      if (halo) row[hs] = staged_rho(st, hs);
     }
+    // barrier B: all reads of the stage slot about to be refilled (row k-3)
+    // are done
     __syncthreads();
+    if (k + PD <= klast) request(k + PD);
+    cp_async_commit();
+    cp_async_wait<PD - 1>();               // row k+1 landed (visible after barrier C)
     if (k - 1 >= y0 - 1) put_mu(k - 1);
     __syncthreads();
     const int c = k - 2;                   // row to collide
@@ -340,21 +393,22 @@ __global__ void __launch_bounds__(kMaxTile)
                     T(1.0 / 12.0) * ((r_up[sx + 1] + r_up[sx - 1]) -
                                      (r_dn[sx + 1] + r_dn[sx - 1]));
       const T rs = r_c[sx];
-      const T* st = stage + (c & (kStages - 1)) * 9 * SW;
-      T g[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) g[i] = st[i * SW + sx];
+      const T* st = stage + slot_of(c) * 9 * SW;
+      // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
+      T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
+                st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
+                st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
       T ux, uy;
       collide<T, WB>(g, rs, gmx, gmy, grx, gry, p, ux, uy);
       if (!MOMENTS) {
-        const long long o = (long long)c * p.pitch + xc;
+        const long long o = (long long)c * p.pitch + x0 + tx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) dst[i * p.plane + o] = g[i];
       } else {
         const double rho = (double)rs + p.rho_ref;
         const double mu = (double)m_c[sx];
         const double dux = (double)ux, duy = (double)uy;
-        const long long kk = (long long)c * p.nx + xc;
+        const long long kk = (long long)c * p.nx + x0 + tx;
         if (mo.rho) mo.rho[kk] = rho;
         if (mo.ux) mo.ux[kk] = dux;
         if (mo.uy) mo.uy[kk] = duy;
@@ -415,8 +469,9 @@ __global__ void __launch_bounds__(kMaxTile)
 }
 
 // Final reduction of the per-CTA records, one block, fixed order.
-// out: mass, kinetic, umax, mu_min, mu_max, nonfinite.
-__global__ void __launch_bounds__(256)
+// out: mass, kinetic, umax, mu_min, mu_max, nonfinite.  (static: every
+// translation unit that includes this header gets its own copy.)
+static __global__ void __launch_bounds__(256)
     stats_finalize_kernel(const double* __restrict__ partials, int n,
                           double* __restrict__ out) {
   __shared__ double red[256][kStatRec];
@@ -456,8 +511,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // Per-direction constants for the layout kernels.
-__constant__ int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__constant__ int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static __constant__ int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static __constant__ int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 // Initial state f_i = f_i^eq(rho, u = 0), stored for pull streaming:
 // P_i(y) = f_i(y + c_i) - s_i.  rest0 / rest_i: the rest equilibrium as
