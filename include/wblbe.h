@@ -177,6 +177,37 @@ wblbe_status wblbe_destroy(wblbe_handle h);
 /* Last error message of h, or of the calling thread when h is NULL. */
 const char* wblbe_last_error(wblbe_handle h);
 
+/* ---- allocation-free statistics pass ------------------------------------
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * cannot allocate device memory at all: code running while a CUDA graph is
+ * being captured, hosts whose own allocator owns the whole device and
+ * forbids cudaMalloc, plug-ins that only receive buffers.  It computes, from
+ * caller-held populations f ([9][ny][nx] float64 on the device, the layout of
+ * wblbe_get_populations), the fields rho, ux, uy, mu ([ny][nx] float64 device
+ * pointers, each may be NULL) and the stats (host pointer, may be NULL;
+ * step and mass_drift_rel are returned as 0), exactly as wblbe_moments does
+ * for a handle holding that state.  params->precision must be WBLBE_FP64.
+ *
+ * It allocates nothing and creates no handle: its only scratch is a fixed
+ * array inside the library (16385 records of 6 float64, about 786 KB), which
+ * every GPU that loads the library holds until the process exits.  Lattices
+ * needing more than ceil(nx/32) * ceil(ny/8) = 16384 records (for example
+ * 4096 x 4096 needs 65536; 1024 x 1024 needs 4096) are rejected with
+ * WBLBE_ENOMEM.  The first call on a device looks up that device's address
+ * of the array (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (different streams, or different host threads on one device) race and
+ * must be serialised by the caller.  Work is issued on cuda_stream (NULL =
+ * legacy default stream); when stats is not NULL the call synchronises that
+ * stream.  Errors: EINVAL (NULL params/f, invalid parameters, precision not
+ * FP64), ENOMEM (lattice too large for the scratch), ECUDA.  The message of
+ * the last failure on the calling thread is wblbe_noalloc_last_error(). */
+wblbe_status wblbe_moments_noalloc(const wblbe_params* params, const double* f,
+                                   double* rho, double* ux, double* uy,
+                                   double* mu, wblbe_stats* stats,
+                                   void* cuda_stream);
+const char* wblbe_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

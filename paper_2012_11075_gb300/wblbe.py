@@ -77,6 +77,9 @@ _SIGNATURES = {
     "wblbe_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_destroy": (ctypes.c_int, [_H]),
     "wblbe_last_error": (ctypes.c_char_p, [_H]),
+    "wblbe_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(CParams), _P, _P, _P, _P, _P,
+                                             ctypes.POINTER(CStats), _P]),
+    "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
