@@ -29,7 +29,8 @@
 
 namespace wblbe {
 
-constexpr int kRing = 8;          // rows kept in each shared-memory ring
+constexpr int kRing = 8;          // rows kept in the density ring
+constexpr int kMuRing = 4;        // rows kept in the chemical-potential ring
 constexpr int kHalo = 2;          // density halo radius (mu needs 1, grad mu 2)
 constexpr int kMaxTile = 256;
 
@@ -78,6 +79,11 @@ __device__ __forceinline__ T chem_pot(T c, T e, T w, T n, T s, T ne, T nw, T se,
   return mu0 - kappa * lap;
 }
 
+// 1/x: correctly rounded reciprocal in FP32 (cheaper than a division), the
+// plain IEEE division in FP64.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Collision of one node in stored variables.  Inputs: the nine pulled
 // populations g, the stored density rs (rho = rs + rho_ref), gradients of mu
 // and rho.  Outputs: the nine post-collision stored populations (into g) and
@@ -107,7 +113,7 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   }
   const T jx = ((g[1] - g[3]) + (g[5] - g[7])) + (g[8] - g[6]);
   const T jy = ((g[2] - g[4]) + (g[5] - g[7])) + (g[6] - g[8]);
-  const T inv_rho = T(1) / rho;
+  const T inv_rho = recip(rho);
   const T ux = (jx + T(0.5) * Fx) * inv_rho;            // Eq. rhoU
   const T uy = (jy + T(0.5) * Fy) * inv_rho;
   ux_out = ux;
@@ -212,14 +218,23 @@ __host__ __device__ constexpr int dir_cy(int i) {
 // Rows of populations staged in shared memory: the pipeline keeps the row
 // being collided, the two rows above it, and kStages - 3 rows in flight.
 template <typename T> struct Staging;
-template <> struct Staging<float> { static constexpr int kStages = 8; };
-template <> struct Staging<double> { static constexpr int kStages = 4; };
+// min_blocks(tx): resident CTAs the register budget must allow (64
+// registers per thread in FP32, 128 in FP64), so that shared memory, not
+// registers, sets the occupancy (FP32, 128 columns: 7 CTAs per SM).
+template <> struct Staging<float> {
+  static constexpr int kStages = 5;
+  __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 64); }
+};
+template <> struct Staging<double> {
+  static constexpr int kStages = 4;
+  __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 128); }
+};
 
 constexpr int kPad = 4;   // staged columns on each side of a strip (x0-4 .. x0+TX+3)
 
 __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size_t elem) {
   // 128 bytes of alignment slack + the buffers
-  return 128 + ((size_t)stages * 9 + 2 * kRing) * (size_t)(tile + 2 * kPad) * elem;
+  return 128 + ((size_t)stages * 9 + kRing + kMuRing) * (size_t)(tile + 2 * kPad) * elem;
 }
 
 // The fused step kernel (MOMENTS = false) and the macroscopic-field /
@@ -232,26 +247,30 @@ __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size
 // f_i = stage[slot][i][s - c_ix].
 //
 // Pipeline over the rows k = y0-2 .. y1+1 of a strip (y0..y1-1 are the rows
-// this CTA updates): wait for row k, reduce it to densities (rho ring), request
-// row k + PD, compute mu of row k-1 (mu ring), collide and store row k-2.
+// this CTA updates): reduce row k to densities (rho ring), request row k + PD,
+// compute mu of row k-1 (mu ring), collide and store row k-2.
 //
-// blockDim.x = tile_x; grid = (ceil(nx / tile_x), ceil(ny / rows)).
-// Dynamic shared memory: strip_smem_bytes(tile_x, kStages, sizeof(T)).
-template <typename T, bool WB, bool MOMENTS>
-__global__ void __launch_bounds__(kMaxTile, 1)
+// The strip width TX is a template parameter so that every shared-memory
+// offset is a compile-time constant.
+// blockDim.x = TX; grid = (ceil(nx / TX), ceil(ny / rows)).
+// Dynamic shared memory: strip_smem_bytes(TX, kStages, sizeof(T)).
+template <typename T, bool WB, bool MOMENTS, int TX>
+__global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
   constexpr int kStages = Staging<T>::kStages;
   constexpr int PD = kStages - 3;          // rows requested ahead of use
+  constexpr int SW = TX + 2 * kPad;        // row width of every buffer
+  constexpr int E = 16 / sizeof(T);        // elements per 16-byte chunk
+  constexpr int NCH = SW / E;              // chunks per plane row
+  constexpr int kMaxChunks = (9 * NCH + TX - 1) / TX;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int TX = blockDim.x;
-  const int SW = TX + 2 * kPad;            // row width of every buffer
   // 128-byte aligned base (16-byte copies need 16)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   T* stage = reinterpret_cast<T*>(base);               // [kStages][9][SW]
   T* rho_s = stage + kStages * 9 * SW;                 // [kRing][SW]
-  T* mu_s = rho_s + kRing * SW;                        // [kRing][SW]
+  T* mu_s = rho_s + kRing * SW;                        // [kMuRing][SW]
 
   const int tx = threadIdx.x;
   const int x0 = blockIdx.x * TX;
@@ -267,36 +286,29 @@ __global__ void __launch_bounds__(kMaxTile, 1)
 
   const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa = T(p.kappa);
   const int kfirst = y0 - 2, klast = y1 + 1;
-  auto slot_of = [&](int r) { return (r - kfirst) % kStages; };
 
   // 16-byte chunks this thread copies in every row (fixed per thread): chunk
   // j of plane i covers columns x0-4+jE .. x0-4+jE+E-1, which wrap only as a
-  // whole (nx % 4 == 0).  At most ceil(9 (TX + 8) / E / TX) chunks per
-  // thread: 3 in FP32, 6 in FP64 (TX >= 32).
-  constexpr int E = 16 / sizeof(T);
-  constexpr int kMaxChunks = sizeof(T) == 4 ? 3 : 6;
-  int ch_goff[kMaxChunks], ch_soff[kMaxChunks], ch_cy[kMaxChunks];
-  int nch_mine = 0;
-  if (use_vec) {
-    const int nch = SW / E;
+  // whole (nx % 4 == 0).
+  const T* ch_src[kMaxChunks];
+  int ch_dst[kMaxChunks], ch_dy[kMaxChunks];
+  bool ch_on[kMaxChunks];
 #pragma unroll
-    for (int c = 0; c < kMaxChunks; ++c) {
-      const int q = tx + c * TX;
-      if (q >= 9 * nch) break;
-      const int i = q / nch, j = q - i * nch;
-      int col = x0 - kPad + j * E;
-      if (col < 0) col += p.nx;
-      else if (col >= p.nx) col -= p.nx;
-      ch_goff[c] = col;
-      ch_soff[c] = i * SW + j * E;
-      ch_cy[c] = dir_cy(i) + 1 + 3 * i;          // plane and row selector
-      nch_mine = c + 1;
-    }
+  for (int c = 0; c < kMaxChunks; ++c) {
+    const int q = tx + c * TX;
+    ch_on[c] = use_vec && q < 9 * NCH;
+    const int i = ch_on[c] ? q / NCH : 0, j = ch_on[c] ? q - i * NCH : 0;
+    int col = x0 - kPad + j * E;
+    if (col < 0) col += p.nx;
+    else if (col >= p.nx) col -= p.nx;
+    ch_src[c] = src + i * p.plane + col;
+    ch_dst[c] = i * SW + j * E;
+    ch_dy[c] = dir_cy(i);
   }
 
-  // Request logical row r (its plane rows r - c_iy, columns x0-4 .. x0+w+3).
-  auto request = [&](int r) {
-    T* st = stage + slot_of(r) * 9 * SW;
+  // Request logical row r (its plane rows r - c_iy) into stage slot `slot`.
+  auto request = [&](int r, int slot) {
+    T* st = stage + slot * 9 * SW;
     const int rw = wrap_index(r, p.ny);
     // row offsets for c_iy = -1, 0, +1: rows r+1, r, r-1
     const int row_p = ((rw == p.ny - 1) ? 0 : rw + 1) * p.pitch;
@@ -305,11 +317,9 @@ __global__ void __launch_bounds__(kMaxTile, 1)
     if (use_vec) {
 #pragma unroll
       for (int c = 0; c < kMaxChunks; ++c) {
-        if (c >= nch_mine) break;
-        const int sel = ch_cy[c];
-        const int i = sel / 3, cyi = sel - 3 * i;
-        const int roff = cyi == 0 ? row_p : (cyi == 1 ? row_0 : row_m);
-        cp_async16(st + ch_soff[c], src + i * p.plane + roff + ch_goff[c]);
+        if (!ch_on[c]) continue;
+        const int roff = ch_dy[c] == 0 ? row_0 : (ch_dy[c] > 0 ? row_m : row_p);
+        cp_async16(st + ch_dst[c], ch_src[c] + roff);
       }
     } else {
       const int ncols = w + 2 * kPad;
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(kMaxTile, 1)
     const T* rn = rho_s + ((r + 1) & (kRing - 1)) * SW;  // row above (y+1)
     const T* rc = rho_s + (r & (kRing - 1)) * SW;
     const T* rsb = rho_s + ((r - 1) & (kRing - 1)) * SW; // row below (y-1)
-    T* mrow = mu_s + (r & (kRing - 1)) * SW;
+    T* mrow = mu_s + (r & (kMuRing - 1)) * SW;
     auto at = [&](int s) {
       return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
                          rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa);
@@ -349,8 +359,10 @@ __global__ void __launch_bounds__(kMaxTile, 1)
   double st_mumin = 1e300, st_mumax = -1e300;
   int st_bad = 0;
 
-  for (int r = kfirst; r < kfirst + PD; ++r) {
-    if (r <= klast) request(r);
+  // stage slots: row k at sk, row k+PD at sq, row k-2 at sc (running counters)
+  int sk = 0, sq = PD, sc = kStages - 2;
+  for (int n = 0; n < PD; ++n) {
+    if (kfirst + n <= klast) request(kfirst + n, n);
     cp_async_commit();                     // one group per row, possibly empty
   }
   cp_async_wait<PD - 1>();                 // row kfirst (this thread's copies)
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(kMaxTile, 1)
 
   for (int k = kfirst; k <= klast; ++k) {
     {
-      const T* st = stage + slot_of(k) * 9 * SW;
+      const T* st = stage + sk * 9 * SW;
       T* row = rho_s + (k & (kRing - 1)) * SW;
       if (own) row[sx] = staged_rho(st, sx);
       if (halo) row[hs] = staged_rho(st, hs);
@@ -366,7 +378,7 @@ __global__ void __launch_bounds__(kMaxTile, 1)
     // barrier B: all reads of the stage slot about to be refilled (row k-3)
     // are done
     __syncthreads();
-    if (k + PD <= klast) request(k + PD);
+    if (k + PD <= klast) request(k + PD, sq);
     cp_async_commit();
     cp_async_wait<PD - 1>();               // row k+1 landed (visible after barrier C)
     if (k - 1 >= y0 - 1) put_mu(k - 1);
@@ -376,9 +388,9 @@ __global__ void __launch_bounds__(kMaxTile, 1)
       const T* r_dn = rho_s + ((c - 1) & (kRing - 1)) * SW;
       const T* r_c = rho_s + (c & (kRing - 1)) * SW;
       const T* r_up = rho_s + ((c + 1) & (kRing - 1)) * SW;
-      const T* m_dn = mu_s + ((c - 1) & (kRing - 1)) * SW;
-      const T* m_c = mu_s + (c & (kRing - 1)) * SW;
-      const T* m_up = mu_s + ((c + 1) & (kRing - 1)) * SW;
+      const T* m_dn = mu_s + ((c - 1) & (kMuRing - 1)) * SW;
+      const T* m_c = mu_s + (c & (kMuRing - 1)) * SW;
+      const T* m_up = mu_s + ((c + 1) & (kMuRing - 1)) * SW;
       // grad(phi) = (E - W)/3 + (NE + SE - NW - SW)/12, likewise in y
       const T gmx = T(1.0 / 3.0) * (m_c[sx + 1] - m_c[sx - 1]) +
                     T(1.0 / 12.0) * ((m_up[sx + 1] + m_dn[sx + 1]) -
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(kMaxTile, 1)
                     T(1.0 / 12.0) * ((r_up[sx + 1] + r_up[sx - 1]) -
                                      (r_dn[sx + 1] + r_dn[sx - 1]));
       const T rs = r_c[sx];
-      const T* st = stage + slot_of(c) * 9 * SW;
+      const T* st = stage + sc * 9 * SW;
       // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
       T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
                 st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
@@ -401,9 +413,12 @@ __global__ void __launch_bounds__(kMaxTile, 1)
       T ux, uy;
       collide<T, WB>(g, rs, gmx, gmy, grx, gry, p, ux, uy);
       if (!MOMENTS) {
-        const long long o = (long long)c * p.pitch + x0 + tx;
+        T* out = dst + (long long)c * p.pitch + x0 + tx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) dst[i * p.plane + o] = g[i];
+        for (int i = 0; i < 9; ++i) {
+          *out = g[i];
+          out += p.plane;
+        }
       } else {
         const double rho = (double)rs + p.rho_ref;
         const double mu = (double)m_c[sx];
@@ -422,6 +437,9 @@ __global__ void __launch_bounds__(kMaxTile, 1)
         if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
       }
     }
+    sk = (sk + 1 == kStages) ? 0 : sk + 1;
+    sq = (sq + 1 == kStages) ? 0 : sq + 1;
+    sc = (sc + 1 == kStages) ? 0 : sc + 1;
   }
   cp_async_wait<0>();
 

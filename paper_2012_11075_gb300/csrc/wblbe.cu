@@ -187,36 +187,32 @@ LayoutParams make_layout_params(const wblbe_ctx* h) {
   return lp;
 }
 
-wblbe_launch default_launch(const wblbe_params& p) {
-  wblbe_launch l{};
-  l.tile_x = p.nx >= 128 ? 128 : (p.nx > 32 ? 64 : 32);
-  const long long strips = (p.nx + l.tile_x - 1) / l.tile_x;
-  const long long target = (long long)kNumSMs * 8;   // about one full wave
-  long long rows = (p.ny * strips + target - 1) / target;
-  if (rows < 4) rows = 4;
-  if (rows > 512) rows = 512;
-  if (rows > p.ny) rows = p.ny;
-  l.rows_per_cta = (int)rows;
-  return l;
-}
-
 bool launch_valid(const wblbe_launch* l) {
   if (!l) return false;
   if (l->tile_x != 32 && l->tile_x != 64 && l->tile_x != 128 && l->tile_x != 256) return false;
   return l->rows_per_cta >= 1;
 }
 
-template <typename T, bool WB, bool MOM>
+template <typename T>
 size_t strip_smem(int tile) {
   return strip_smem_bytes(tile, Staging<T>::kStages, sizeof(T));
 }
 
-// Allow every instantiation the dynamic shared memory of the widest tile.
+// Allow every instantiation the dynamic shared memory it launches with.
+template <typename T, bool WB, bool MOM, int TX>
+cudaError_t allow_smem_tx() {
+  return cudaFuncSetAttribute(lbm_strip_kernel<T, WB, MOM, TX>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)strip_smem<T>(TX));
+}
 template <typename T, bool WB, bool MOM>
 cudaError_t allow_smem() {
-  return cudaFuncSetAttribute(lbm_strip_kernel<T, WB, MOM>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)strip_smem<T, WB, MOM>(kMaxTile));
+  cudaError_t e = cudaSuccess, r;
+  if ((r = allow_smem_tx<T, WB, MOM, 32>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, WB, MOM, 64>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, WB, MOM, 128>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, WB, MOM, 256>()) != cudaSuccess) e = r;
+  return e;
 }
 
 cudaError_t allow_smem_all() {
@@ -232,13 +228,70 @@ cudaError_t allow_smem_all() {
   return e;
 }
 
+template <typename T, bool WB, bool MOM, int TX>
+cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
+                      cudaStream_t s) {
+  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + kp.rows - 1) / kp.rows);
+  lbm_strip_kernel<T, WB, MOM, TX><<<grid, TX, strip_smem<T>(TX), s>>>(
+      static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
+  return cudaGetLastError();
+}
+
 template <typename T, bool WB, bool MOM>
 cudaError_t launch_strip(const void* src, void* dst, const KParams& kp,
                          const MomentsOut& mo, int tile, cudaStream_t s) {
-  dim3 grid((kp.nx + tile - 1) / tile, (kp.ny + kp.rows - 1) / kp.rows);
-  lbm_strip_kernel<T, WB, MOM><<<grid, tile, strip_smem<T, WB, MOM>(tile), s>>>(
-      static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
-  return cudaGetLastError();
+  switch (tile) {
+    case 32: return launch_tx<T, WB, MOM, 32>(src, dst, kp, mo, s);
+    case 64: return launch_tx<T, WB, MOM, 64>(src, dst, kp, mo, s);
+    case 128: return launch_tx<T, WB, MOM, 128>(src, dst, kp, mo, s);
+    case 256: return launch_tx<T, WB, MOM, 256>(src, dst, kp, mo, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Resident CTAs per SM of the step kernel at this tile width.
+template <typename T, bool WB, int TX>
+int resident_tx() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_strip_kernel<T, WB, false, TX>, TX,
+                                                    strip_smem<T>(TX)) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+template <typename T, bool WB>
+int resident_per_sm(int tile) {
+  switch (tile) {
+    case 32: return resident_tx<T, WB, 32>();
+    case 64: return resident_tx<T, WB, 64>();
+    case 128: return resident_tx<T, WB, 128>();
+    default: return resident_tx<T, WB, 256>();
+  }
+}
+
+// Default launch shape: 128-column strips (narrower lattices: 64 or 32), and
+// rows per CTA chosen so that the whole grid is resident at once (one wave),
+// with at least 8 rows per CTA (each CTA re-reads 4 halo rows).
+wblbe_launch default_launch(const wblbe_params& p) {
+  wblbe_launch l{};
+  l.tile_x = p.nx >= 128 ? 128 : (p.nx > 32 ? 64 : 32);
+  int nsm = kNumSMs, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool wb = p.scheme == WBLBE_WELL_BALANCED;
+  int per_sm;
+  if (p.precision == WBLBE_FP64)
+    per_sm = wb ? resident_per_sm<double, true>(l.tile_x) : resident_per_sm<double, false>(l.tile_x);
+  else
+    per_sm = wb ? resident_per_sm<float, true>(l.tile_x) : resident_per_sm<float, false>(l.tile_x);
+  const long long resident = (long long)per_sm * nsm;
+  const long long strips = (p.nx + l.tile_x - 1) / l.tile_x;
+  long long segs = resident / strips;
+  if (segs < 1) segs = 1;
+  long long rows = (p.ny + segs - 1) / segs;
+  if (rows < 8) rows = 8;
+  if (rows > p.ny) rows = p.ny;
+  l.rows_per_cta = (int)rows;
+  return l;
 }
 
 cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
