@@ -69,20 +69,38 @@ __device__ __forceinline__ int wrap_index(int a, int n) {
 // stored densities rs (rho = rs + rho_ref):
 //   mu_0 = 2 beta (rho - rho_l)(rho - rho_g)(2 rho - rho_l - rho_g)
 //   lap  = [4 (E + W + N + S) + (NE + NW + SE + SW) - 20 C] / 6
+// kappa6 = kappa / 6.
 template <typename T>
 __device__ __forceinline__ T chem_pot(T c, T e, T w, T n, T s, T ne, T nw, T se,
-                                      T sw, T two_beta, T dl, T dg, T kappa) {
+                                      T sw, T two_beta, T dl, T dg, T kappa6) {
   T a = c + dl, b = c + dg;
   T mu0 = two_beta * a * b * (a + b);
-  T lap = (T(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - T(20) * c) *
-          T(1.0 / 6.0);
-  return mu0 - kappa * lap;
+  T lap6 = T(4) * ((e + w) + (n + s)) + ((ne + nw) + (se + sw)) - T(20) * c;
+  return mu0 - kappa6 * lap6;
 }
 
-// 1/x: correctly rounded reciprocal in FP32 (cheaper than a division), the
-// plain IEEE division in FP64.
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// 1/x: the hardware reciprocal approximation in FP32 (about 1 ulp; the FP32
+// path's error budget is set by float storage anyway), the IEEE division in
+// FP64.
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// Collision constants in the arithmetic type, converted once per kernel (a
+// float <- double conversion inside the row loop would run on the FP64 pipe).
+// In FP32-shifted storage the rho0 terms of the well-balanced equilibrium
+// cancel against the shift, so only FP64 carries them.
+template <typename T>
+struct CollideConsts {
+  T omega, kf, keep, kf_m3, rho_ref, wb_b0c, om_bax, om_bdg;
+  __device__ explicit CollideConsts(const KParams& p)
+      : omega(T(p.omega)), kf(T(p.kforce)), keep(T(1.0 - p.omega)), kf_m3(T(-3.0 * p.kforce)),
+        rho_ref(T(p.rho_ref)), wb_b0c(T(p.wb_b0c)), om_bax(T(p.omega * p.wb_bax)),
+        om_bdg(T(p.omega * p.wb_bdg)) {}
+};
 
 // Collision of one node in stored variables.  Inputs: the nine pulled
 // populations g, the stored density rs (rho = rs + rho_ref), gradients of mu
@@ -96,13 +114,17 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // with G = F + cs^2 grad rho, h_i = (3|c_i|^2 - 2)/2 for the well-balanced
 // scheme (Eq. mFi) and G = F, h_i = 0 for the standard one (Eq. Fi).  Each
 // pair of opposite directions shares the even part E and flips the odd
-// part O of  omega feq_i + kforce F_i.
+// part O of  omega feq_i + kforce F_i.  With t = omega rho (-3/2 u.u) +
+// kforce (-3 u.G) and k_u = kforce (u.grad rho):
+//   E_0 = w_0 (t - k_u) + omega b_0,   E_axis base = w_ax (t + k_u/2) + omega b_ax,
+//   E_diag base = w_dg (t + 2 k_u) + omega b_dg.
 template <typename T, bool WB>
 __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
-                                        T gry, const KParams& p, T& ux_out,
+                                        T gry, const CollideConsts<T>& q, T& ux_out,
                                         T& uy_out) {
-  const T omega = T(p.omega), kf = T(p.kforce);
-  const T rho = rs + T(p.rho_ref);
+  constexpr bool kShifted = sizeof(T) == 4;   // FP32 storage is always shifted
+  const T omega = q.omega, kf = q.kf;
+  const T rho = rs + q.rho_ref;
   T Fx, Fy;
   if (WB) {
     Fx = -rho * gmx;                                     // Eq. mF
@@ -111,63 +133,65 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
     Fx = T(1.0 / 3.0) * grx - rho * gmx;                 // potential form
     Fy = T(1.0 / 3.0) * gry - rho * gmy;
   }
-  const T jx = ((g[1] - g[3]) + (g[5] - g[7])) + (g[8] - g[6]);
-  const T jy = ((g[2] - g[4]) + (g[5] - g[7])) + (g[6] - g[8]);
+  const T d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d86 = g[8] - g[6];
+  const T jx = (d13 + d57) + d86;
+  const T jy = (d24 + d57) - d86;
   const T inv_rho = recip(rho);
   const T ux = (jx + T(0.5) * Fx) * inv_rho;            // Eq. rhoU
   const T uy = (jy + T(0.5) * Fy) * inv_rho;
   ux_out = ux;
   uy_out = uy;
 
-  T Gx = Fx, Gy = Fy, ugr = T(0);
+  T Gx = Fx, Gy = Fy;
   if (WB) {
     Gx = Fx + T(1.0 / 3.0) * grx;
     Gy = Fy + T(1.0 / 3.0) * gry;
-    ugr = ux * grx + uy * gry;
   }
-  const T uu = ux * ux + uy * uy;
-  const T A = T(-1.5) * uu;                  // -3/2 u.u
-  const T B = T(-3) * (ux * Gx + uy * Gy);   // -3 u.G
   const T orho = omega * rho;
+  const T uu = ux * ux + uy * uy;
+  const T uG = ux * Gx + uy * Gy;
+  const T t = (T(-1.5) * orho) * uu + q.kf_m3 * uG;
 
-  // base terms
-  T b0, bax, bdg;
+  T E0, Cax, Cdg;
   if (WB) {
-    b0 = rs - T(p.wb_b0c);
-    bax = T(p.wb_bax);
-    bdg = T(p.wb_bdg);
+    const T ku = kf * (ux * grx + uy * gry);
+    E0 = T(4.0 / 9.0) * (t - ku);
+    Cax = T(1.0 / 9.0) * (t + T(0.5) * ku);
+    Cdg = T(1.0 / 36.0) * (t + T(2) * ku);
+    if (kShifted) {
+      E0 = E0 + omega * rs;                            // b_0 = rs, b_ax = b_dg = 0
+    } else {
+      E0 = E0 + omega * (rs - q.wb_b0c);
+      Cax = Cax + q.om_bax;
+      Cdg = Cdg + q.om_bdg;
+    }
   } else {
-    b0 = T(4.0 / 9.0) * rs;
-    bax = T(1.0 / 9.0) * rs;
-    bdg = T(1.0 / 36.0) * rs;
+    const T s = t + omega * rs;                        // b_i = w_i rs
+    E0 = T(4.0 / 9.0) * s;
+    Cax = T(1.0 / 9.0) * s;
+    Cdg = T(1.0 / 36.0) * s;
   }
-  const T keep = T(1) - omega;
-
-  // rest direction: w0 = 4/9, h0 = -1 (WB)
-  const T E0 = omega * b0 + T(4.0 / 9.0) * (orho * A + kf * (B - ugr));
-  // axis directions: w = 1/9, h = 1/2 (WB)
-  const T Cax = omega * bax + T(1.0 / 9.0) * (orho * A + kf * (B + T(0.5) * ugr));
-  // diagonal directions: w = 1/36, h = 2 (WB)
-  const T Cdg = omega * bdg + T(1.0 / 36.0) * (orho * A + kf * (B + T(2) * ugr));
   const T hrho = T(0.5) * orho;              // (omega rho / 9) * 9/2
+  const T kGx = kf * Gx, kGy = kf * Gy;
   const T Mx = orho * ux + kf * Fx;          // odd parts: omega rho c.u + kf c.F
   const T My = orho * uy + kf * Fy;
 
   // pair (1,3): c = (1,0)
-  const T E1 = Cax + ux * (hrho * ux + kf * Gx);
+  const T E1 = Cax + ux * (hrho * ux + kGx);
   const T O1 = T(1.0 / 3.0) * Mx;
   // pair (2,4): c = (0,1)
-  const T E2 = Cax + uy * (hrho * uy + kf * Gy);
+  const T E2 = Cax + uy * (hrho * uy + kGy);
   const T O2 = T(1.0 / 3.0) * My;
   // pair (5,7): c = (1,1)
-  const T cu5 = ux + uy, cG5 = Gx + Gy;
-  const T E5 = Cdg + T(0.25) * cu5 * (hrho * cu5 + kf * cG5);
+  const T cu5 = ux + uy;
+  const T E5 = Cdg + (T(0.25) * cu5) * (hrho * cu5 + (kGx + kGy));
   const T O5 = T(1.0 / 12.0) * (Mx + My);
   // pair (6,8): c = (-1,1)
-  const T cu6 = uy - ux, cG6 = Gy - Gx;
-  const T E6 = Cdg + T(0.25) * cu6 * (hrho * cu6 + kf * cG6);
+  const T cu6 = uy - ux;
+  const T E6 = Cdg + (T(0.25) * cu6) * (hrho * cu6 + (kGy - kGx));
   const T O6 = T(1.0 / 12.0) * (My - Mx);
 
+  const T keep = q.keep;
   g[0] = keep * g[0] + E0;
   g[1] = keep * g[1] + (E1 + O1);
   g[3] = keep * g[3] + (E1 - O1);
@@ -177,6 +201,18 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   g[7] = keep * g[7] + (E5 - O5);
   g[6] = keep * g[6] + (E6 + O6);
   g[8] = keep * g[8] + (E6 - O6);
+}
+
+// Isotropic central gradient from the 3x3 neighbourhood:
+//   grad_x = (E - W)/3 + (NE + SE - NW - SW)/12,
+//   grad_y = (N - S)/3 + (NE + NW - SE - SW)/12,
+// written with the diagonal differences d1 = NE - SW, d2 = SE - NW.
+template <typename T>
+__device__ __forceinline__ void iso_grad(T e, T w, T n, T s, T ne, T nw, T se, T sw,
+                                         T& gx, T& gy) {
+  const T d1 = ne - sw, d2 = se - nw;
+  gx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * (d1 + d2);
+  gy = T(1.0 / 3.0) * (n - s) + T(1.0 / 12.0) * (d1 - d2);
 }
 
 // ---- asynchronous copies into shared memory -------------------------------
@@ -215,18 +251,22 @@ __host__ __device__ constexpr int dir_cy(int i) {
   return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
 
-// Rows of populations staged in shared memory: the pipeline keeps the row
-// being collided, the two rows above it, and kStages - 3 rows in flight.
+// Staging: each loop iteration advances kRows lattice rows per thread; the
+// stage keeps the rows being collided (two behind the density front), the
+// kRows rows being reduced to densities, and kAhead groups of kRows rows in
+// flight.  min_blocks(tx): resident CTAs the register budget must allow, so
+// that shared memory, not registers, sets the occupancy.
 template <typename T> struct Staging;
-// min_blocks(tx): resident CTAs the register budget must allow (64
-// registers per thread in FP32, 128 in FP64), so that shared memory, not
-// registers, sets the occupancy (FP32, 128 columns: 7 CTAs per SM).
 template <> struct Staging<float> {
-  static constexpr int kStages = 5;
-  __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 64); }
+  static constexpr int kRows = 2;
+  static constexpr int kAhead = 2;
+  static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 8
+  __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 128); }
 };
 template <> struct Staging<double> {
-  static constexpr int kStages = 4;
+  static constexpr int kRows = 1;
+  static constexpr int kAhead = 1;
+  static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 4
   __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 128); }
 };
 
@@ -247,8 +287,11 @@ __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size
 // f_i = stage[slot][i][s - c_ix].
 //
 // Pipeline over the rows k = y0-2 .. y1+1 of a strip (y0..y1-1 are the rows
-// this CTA updates): reduce row k to densities (rho ring), request row k + PD,
-// compute mu of row k-1 (mu ring), collide and store row k-2.
+// this CTA updates), kRows rows per iteration: reduce rows k.. to densities
+// (rho ring), request the rows kRows * kAhead further on, compute mu of rows
+// k-1.. (mu ring), collide and store rows k-2..  Two rows per iteration in
+// FP32 halve the per-row barrier and loop overhead and share the stencil
+// loads of neighbouring rows.
 //
 // The strip width TX is a template parameter so that every shared-memory
 // offset is a compile-time constant.
@@ -258,8 +301,9 @@ template <typename T, bool WB, bool MOMENTS, int TX>
 __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
+  constexpr int R = Staging<T>::kRows;     // rows per iteration
+  constexpr int PDG = Staging<T>::kAhead;  // row groups requested ahead of use
   constexpr int kStages = Staging<T>::kStages;
-  constexpr int PD = kStages - 3;          // rows requested ahead of use
   constexpr int SW = TX + 2 * kPad;        // row width of every buffer
   constexpr int E = 16 / sizeof(T);        // elements per 16-byte chunk
   constexpr int NCH = SW / E;              // chunks per plane row
@@ -279,12 +323,16 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   const int y1 = min(y0 + p.rows, p.ny);
   const bool own = tx < w;
   const int sx = tx + kPad;                // slot of the own column
-  // density halo: slots 2, 3 (x0-2, x0-1) and w+4, w+5 (x0+w, x0+w+1)
+  // Halo work, kept in warp 0 (threads 0-3 take the densities of slots 2, 3
+  // (x0-2, x0-1) and w+4, w+5 (x0+w, x0+w+1); threads 0 and 1 take mu at
+  // slots 3 and w+4): one warp runs the halo branch instead of all of them.
   const bool halo = tx < 4;
   const int hs = tx < 2 ? 2 + tx : w + 2 + tx;
+  const int mu_lo = 0, mu_hi = 1;
   const bool use_vec = (w == TX) && (p.nx % 4 == 0);
 
-  const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa = T(p.kappa);
+  const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa6 = T(p.kappa / 6.0);
+  const CollideConsts<T> cc(p);
   const int kfirst = y0 - 2, klast = y1 + 1;
 
   // 16-byte chunks this thread copies in every row (fixed per thread): chunk
@@ -306,14 +354,15 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     ch_dy[c] = dir_cy(i);
   }
 
-  // Request logical row r (its plane rows r - c_iy) into stage slot `slot`.
-  auto request = [&](int r, int slot) {
+  // Request the next logical row (its plane rows r - c_iy) into stage slot
+  // `slot`.  Rows are requested in order kfirst, kfirst+1, ...; the wrapped
+  // row index and the offsets of rows r+1, r, r-1 advance incrementally.
+  int req_rw = wrap_index(kfirst, p.ny);
+  int row_p = ((req_rw == p.ny - 1) ? 0 : req_rw + 1) * p.pitch;
+  int row_0 = req_rw * p.pitch;
+  int row_m = ((req_rw == 0) ? p.ny - 1 : req_rw - 1) * p.pitch;
+  auto request_next = [&](int slot) {
     T* st = stage + slot * 9 * SW;
-    const int rw = wrap_index(r, p.ny);
-    // row offsets for c_iy = -1, 0, +1: rows r+1, r, r-1
-    const int row_p = ((rw == p.ny - 1) ? 0 : rw + 1) * p.pitch;
-    const int row_0 = rw * p.pitch;
-    const int row_m = ((rw == 0) ? p.ny - 1 : rw - 1) * p.pitch;
     if (use_vec) {
 #pragma unroll
       for (int c = 0; c < kMaxChunks; ++c) {
@@ -332,6 +381,10 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
         }
       }
     }
+    req_rw = (req_rw + 1 == p.ny) ? 0 : req_rw + 1;
+    row_m = row_0;
+    row_0 = row_p;
+    row_p = ((req_rw + 1 == p.ny) ? 0 : req_rw + 1) * p.pitch;
   };
   // density of the staged row at slot s: sum_i f_i, f_i = stage[i][s - c_ix]
   auto staged_rho = [&](const T* st, int s) {
@@ -339,8 +392,8 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
            ((st[4 * SW + s] + st[5 * SW + s - 1]) + (st[6 * SW + s + 1] + st[7 * SW + s + 1])) +
            st[8 * SW + s - 1];
   };
-  // mu of logical row r at slots 3 .. w+4 (own slot; threads 0 and 1 also
-  // take slots 3 and w+4).
+  // mu of logical row r at slots 3 .. w+4 (own slot; threads mu_lo and
+  // mu_hi also take slots 3 and w+4).
   auto put_mu = [&](int r) {
     const T* rn = rho_s + ((r + 1) & (kRing - 1)) * SW;  // row above (y+1)
     const T* rc = rho_s + (r & (kRing - 1)) * SW;
@@ -348,98 +401,122 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     T* mrow = mu_s + (r & (kMuRing - 1)) * SW;
     auto at = [&](int s) {
       return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
-                         rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa);
+                         rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
     };
     if (own) mrow[sx] = at(sx);
-    if (tx == 0) mrow[3] = at(3);
-    if (tx == 1) mrow[w + 4] = at(w + 4);
+    if (tx == mu_lo) mrow[3] = at(3);
+    if (tx == mu_hi) mrow[w + 4] = at(w + 4);
   };
 
   double st_mass = 0.0, st_kin = 0.0, st_u2 = 0.0;
   double st_mumin = 1e300, st_mumax = -1e300;
   int st_bad = 0;
 
-  // stage slots: row k at sk, row k+PD at sq, row k-2 at sc (running counters)
-  int sk = 0, sq = PD, sc = kStages - 2;
-  for (int n = 0; n < PD; ++n) {
-    if (kfirst + n <= klast) request(kfirst + n, n);
-    cp_async_commit();                     // one group per row, possibly empty
+  // Rows kfirst .. klast2 are processed in groups of R (klast2 >= klast; a
+  // row past klast only feeds values nobody reads).
+  const int ngroups = (klast - kfirst + R) / R;
+  const int klast2 = kfirst + R * ngroups - 1;
+  auto wrap_slot = [](int sl) { return sl >= kStages ? sl - kStages : sl; };
+
+  // running output positions of the next row to collide
+  T* out_row = dst + (long long)y0 * p.pitch + x0 + tx;
+  long long mom_row = (long long)y0 * p.nx + x0 + tx;
+
+  int sq = 0;                              // stage slot of the next requested row
+  for (int gq = 0; gq < PDG; ++gq) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (kfirst + gq * R + j <= klast2) request_next(sq);
+      sq = wrap_slot(sq + 1);
+    }
+    cp_async_commit();                     // one group per R rows, possibly empty
   }
-  cp_async_wait<PD - 1>();                 // row kfirst (this thread's copies)
+  cp_async_wait<PDG - 1>();                // first group landed (this thread)
   __syncthreads();                         // ... and everyone else's
 
-  for (int k = kfirst; k <= klast; ++k) {
-    {
-      const T* st = stage + sk * 9 * SW;
-      T* row = rho_s + (k & (kRing - 1)) * SW;
+  int sk = 0;                              // stage slot of row k
+  int sc = kStages - 2;                    // stage slot of row k - 2
+  for (int k = kfirst; k <= klast2; k += R) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const T* st = stage + wrap_slot(sk + j) * 9 * SW;
+      T* row = rho_s + ((k + j) & (kRing - 1)) * SW;
       if (own) row[sx] = staged_rho(st, sx);
       if (halo) row[hs] = staged_rho(st, hs);
     }
-    // barrier B: all reads of the stage slot about to be refilled (row k-3)
-    // are done
+    // barrier B: every read of the stage slots about to be refilled (rows
+    // collided an iteration ago) is done
     __syncthreads();
-    if (k + PD <= klast) request(k + PD, sq);
-    cp_async_commit();
-    cp_async_wait<PD - 1>();               // row k+1 landed (visible after barrier C)
-    if (k - 1 >= y0 - 1) put_mu(k - 1);
-    __syncthreads();
-    const int c = k - 2;                   // row to collide
-    if (c >= y0 && own) {
-      const T* r_dn = rho_s + ((c - 1) & (kRing - 1)) * SW;
-      const T* r_c = rho_s + (c & (kRing - 1)) * SW;
-      const T* r_up = rho_s + ((c + 1) & (kRing - 1)) * SW;
-      const T* m_dn = mu_s + ((c - 1) & (kMuRing - 1)) * SW;
-      const T* m_c = mu_s + (c & (kMuRing - 1)) * SW;
-      const T* m_up = mu_s + ((c + 1) & (kMuRing - 1)) * SW;
-      // grad(phi) = (E - W)/3 + (NE + SE - NW - SW)/12, likewise in y
-      const T gmx = T(1.0 / 3.0) * (m_c[sx + 1] - m_c[sx - 1]) +
-                    T(1.0 / 12.0) * ((m_up[sx + 1] + m_dn[sx + 1]) -
-                                     (m_up[sx - 1] + m_dn[sx - 1]));
-      const T gmy = T(1.0 / 3.0) * (m_up[sx] - m_dn[sx]) +
-                    T(1.0 / 12.0) * ((m_up[sx + 1] + m_up[sx - 1]) -
-                                     (m_dn[sx + 1] + m_dn[sx - 1]));
-      const T grx = T(1.0 / 3.0) * (r_c[sx + 1] - r_c[sx - 1]) +
-                    T(1.0 / 12.0) * ((r_up[sx + 1] + r_dn[sx + 1]) -
-                                     (r_up[sx - 1] + r_dn[sx - 1]));
-      const T gry = T(1.0 / 3.0) * (r_up[sx] - r_dn[sx]) +
-                    T(1.0 / 12.0) * ((r_up[sx + 1] + r_up[sx - 1]) -
-                                     (r_dn[sx + 1] + r_dn[sx - 1]));
-      const T rs = r_c[sx];
-      const T* st = stage + sc * 9 * SW;
-      // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
-      T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
-                st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
-                st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
-      T ux, uy;
-      collide<T, WB>(g, rs, gmx, gmy, grx, gry, p, ux, uy);
-      if (!MOMENTS) {
-        T* out = dst + (long long)c * p.pitch + x0 + tx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          *out = g[i];
-          out += p.plane;
+    for (int j = 0; j < R; ++j) {
+      if (k + R * PDG + j <= klast2) request_next(sq);
+      sq = wrap_slot(sq + 1);
+    }
+    cp_async_commit();
+    cp_async_wait<PDG - 1>();              // next group landed (visible after barrier C)
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (k - 1 + j >= y0 - 1) put_mu(k - 1 + j);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int c = k - 2 + j;             // row to collide
+      if (c >= y0 && c < y1 && own) {
+        const T* r_dn = rho_s + ((c - 1) & (kRing - 1)) * SW;
+        const T* r_c = rho_s + (c & (kRing - 1)) * SW;
+        const T* r_up = rho_s + ((c + 1) & (kRing - 1)) * SW;
+        const T* m_dn = mu_s + ((c - 1) & (kMuRing - 1)) * SW;
+        const T* m_c = mu_s + (c & (kMuRing - 1)) * SW;
+        const T* m_up = mu_s + ((c + 1) & (kMuRing - 1)) * SW;
+        // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
+        T gmx, gmy, grx, gry;
+        iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1], m_up[sx - 1],
+                    m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
+        iso_grad<T>(r_c[sx + 1], r_c[sx - 1], r_up[sx], r_dn[sx], r_up[sx + 1], r_up[sx - 1],
+                    r_dn[sx + 1], r_dn[sx - 1], grx, gry);
+        const T rs = r_c[sx];
+        const T* st = stage + wrap_slot(sc + j) * 9 * SW;
+        // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
+        T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
+                  st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
+                  st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
+        T ux, uy;
+        collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+        if (!MOMENTS) {
+          T* out = out_row + (long long)j * p.pitch;
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            *out = g[i];
+            out += p.plane;
+          }
+        } else {
+          const double rho = (double)rs + p.rho_ref;
+          const double mu = (double)m_c[sx];
+          const double dux = (double)ux, duy = (double)uy;
+          const long long kk = mom_row + (long long)j * p.nx;
+          if (mo.rho) mo.rho[kk] = rho;
+          if (mo.ux) mo.ux[kk] = dux;
+          if (mo.uy) mo.uy[kk] = duy;
+          if (mo.mu) mo.mu[kk] = mu;
+          const double u2 = dux * dux + duy * duy;
+          st_mass += rho;
+          st_kin += 0.5 * rho * u2;
+          st_u2 = fmax(st_u2, u2);
+          st_mumin = fmin(st_mumin, mu);
+          st_mumax = fmax(st_mumax, mu);
+          if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
         }
-      } else {
-        const double rho = (double)rs + p.rho_ref;
-        const double mu = (double)m_c[sx];
-        const double dux = (double)ux, duy = (double)uy;
-        const long long kk = (long long)c * p.nx + x0 + tx;
-        if (mo.rho) mo.rho[kk] = rho;
-        if (mo.ux) mo.ux[kk] = dux;
-        if (mo.uy) mo.uy[kk] = duy;
-        if (mo.mu) mo.mu[kk] = mu;
-        const double u2 = dux * dux + duy * duy;
-        st_mass += rho;
-        st_kin += 0.5 * rho * u2;
-        st_u2 = fmax(st_u2, u2);
-        st_mumin = fmin(st_mumin, mu);
-        st_mumax = fmax(st_mumax, mu);
-        if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
       }
     }
-    sk = (sk + 1 == kStages) ? 0 : sk + 1;
-    sq = (sq + 1 == kStages) ? 0 : sq + 1;
-    sc = (sc + 1 == kStages) ? 0 : sc + 1;
+    // advance the output positions by the rows collided in this iteration
+    {
+      const int c0 = k - 2;
+      const int ndone = max(0, min(c0 + R, y1) - max(c0, y0));
+      out_row += (long long)ndone * p.pitch;
+      mom_row += (long long)ndone * p.nx;
+    }
+    sk = wrap_slot(sk + R);
+    sc = wrap_slot(sc + R);
   }
   cp_async_wait<0>();
 

@@ -73,13 +73,13 @@ __global__ void __launch_bounds__(kTileX* kTileY)
     rho_s[ly][lx] = s;
   }
   __syncthreads();
-  const double two_beta = p.two_beta, dl = p.dl, dg = p.dg, kappa = p.kappa;
+  const double two_beta = p.two_beta, dl = p.dl, dg = p.dg, kappa6 = p.kappa / 6.0;
   for (int q = t; q < (kTileY + 2) * (kTileX + 2); q += kTileX * kTileY) {
     const int ly = q / (kTileX + 2) + 1, lx = q % (kTileX + 2) + 1;
     mu_s[ly - 1][lx - 1] = chem_pot<double>(
         rho_s[ly][lx], rho_s[ly][lx + 1], rho_s[ly][lx - 1], rho_s[ly + 1][lx],
         rho_s[ly - 1][lx], rho_s[ly + 1][lx + 1], rho_s[ly + 1][lx - 1],
-        rho_s[ly - 1][lx + 1], rho_s[ly - 1][lx - 1], two_beta, dl, dg, kappa);
+        rho_s[ly - 1][lx + 1], rho_s[ly - 1][lx - 1], two_beta, dl, dg, kappa6);
   }
   __syncthreads();
 
@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(kTileX* kTileY)
     for (int i = 0; i < 9; ++i) g[i] = f[i * plane + k];
     const double rs = rho_s[ry][rx];
     double ux, uy;
-    collide<double, WB>(g, rs, gmx, gmy, grx, gry, p, ux, uy);
+    const CollideConsts<double> cc(p);
+    collide<double, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
     const double mu = mu_s[my][mx];
     if (rho_out) rho_out[k] = rs;
     if (ux_out) ux_out[k] = ux;
