@@ -93,13 +93,25 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // float <- double conversion inside the row loop would run on the FP64 pipe).
 // In FP32-shifted storage the rho0 terms of the well-balanced equilibrium
 // cancel against the shift, so only FP64 carries them.
+// keep = 1 - omega must hold exactly in the arithmetic type: the update
+// keep * g + omega * (...) conserves mass only if keep + omega == 1, and a
+// rounded pair would scale the mass every step.  For omega >= 1/2 (tau <= 2)
+// 1 - omega is exact (Sterbenz); for smaller omega, omega is taken as 1 - keep.
 template <typename T>
 struct CollideConsts {
   T omega, kf, keep, kf_m3, rho_ref, wb_b0c, om_bax, om_bdg;
   __device__ explicit CollideConsts(const KParams& p)
-      : omega(T(p.omega)), kf(T(p.kforce)), keep(T(1.0 - p.omega)), kf_m3(T(-3.0 * p.kforce)),
-        rho_ref(T(p.rho_ref)), wb_b0c(T(p.wb_b0c)), om_bax(T(p.omega * p.wb_bax)),
-        om_bdg(T(p.omega * p.wb_bdg)) {}
+      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)),
+        wb_b0c(T(p.wb_b0c)), om_bax(T(p.omega * p.wb_bax)), om_bdg(T(p.omega * p.wb_bdg)) {
+    const T w = T(p.omega);
+    if (w >= T(0.5)) {
+      omega = w;
+      keep = T(1) - w;
+    } else {
+      keep = T(1.0 - p.omega);
+      omega = T(1) - keep;
+    }
+  }
 };
 
 // Collision of one node in stored variables.  Inputs: the nine pulled
@@ -192,7 +204,6 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   const T O6 = T(1.0 / 12.0) * (My - Mx);
 
   const T keep = q.keep;
-  g[0] = keep * g[0] + E0;
   g[1] = keep * g[1] + (E1 + O1);
   g[3] = keep * g[3] + (E1 - O1);
   g[2] = keep * g[2] + (E2 + O2);
@@ -201,6 +212,18 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   g[7] = keep * g[7] + (E5 - O5);
   g[6] = keep * g[6] + (E6 + O6);
   g[8] = keep * g[8] + (E6 - O6);
+  if (kShifted) {
+    // The collision conserves the node's mass: sum_i g_i' = rs (exactly, in
+    // real arithmetic).  In float storage the rest population g_0 ~ rho -
+    // rho_ref is large, and the small one-signed O(u^2) part of E0 would be
+    // lost to rounding when added to it, while the matching corrections to
+    // the small moving populations survive: a systematic mass gain.  Taking
+    // g_0' from the mass balance leaves only unbiased rounding.
+    (void)E0;
+    g[0] = rs - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+  } else {
+    g[0] = keep * g[0] + E0;
+  }
 }
 
 // Isotropic central gradient from the 3x3 neighbourhood:
