@@ -177,6 +177,112 @@ wblbe_status wblbe_destroy(wblbe_handle h);
 /* Last error message of h, or of the calling thread when h is NULL. */
 const char* wblbe_last_error(wblbe_handle h);
 
+/* ---- batched cases and serving -------------------------------------------
+ * A batch keeps many independent cases (each its own lattice size and
+ * parameters, one scheme and precision for the whole batch) resident on the
+ * device and advances all running cases together with one persistent kernel
+ * per launch: the cases are cut into tiles of tile_x columns by about
+ * rows_per_tile rows; a launch advances every running case by
+ * steps_per_launch steps, tiles waiting (bounded) only for the neighbouring
+ * tiles their halo reads.  Results are bit-identical to a wblbe_create
+ * handle run alone.  Launches are replayed from a captured CUDA graph.
+ * Memory: one caller workspace = control region + arena; each admitted case
+ * takes wblbe_batch_case_bytes() of the arena until it is retired. */
+typedef struct wblbe_batch* wblbe_batch_handle;
+
+typedef struct {
+  int32_t tile_x;            /* 32, 64, 128 or 256                         */
+  int32_t rows_per_tile;     /* >= 4; rows are split into near-equal runs  */
+  int32_t steps_per_launch;  /* >= 1 lattice steps per persistent launch   */
+} wblbe_batch_config;
+
+enum {
+  WBLBE_CASE_RUNNING = 0,    /* being advanced                             */
+  WBLBE_CASE_CONVERGED = 1,  /* max|u| fell below its tolerance            */
+  WBLBE_CASE_MAXSTEPS = 2,   /* reached its step budget                    */
+  WBLBE_CASE_UNSTABLE = 3    /* a non-finite value appeared                */
+};
+
+typedef struct {
+  int64_t case_id;
+  int32_t state;             /* WBLBE_CASE_*                               */
+  int64_t steps;
+  wblbe_stats stats;         /* at the last check (end of a launch group)  */
+} wblbe_case_info;
+
+/* Workspace bytes for a batch: control region for max_cases cases,
+ * max_tiles tiles, cases of at most max_case_nodes nodes, plus arena_bytes of
+ * arena.  0 on invalid arguments. */
+size_t wblbe_batch_workspace_bytes(int32_t max_cases, int32_t max_tiles,
+                                   int64_t max_case_nodes, size_t arena_bytes);
+
+/* Arena bytes one case needs (two buffers with ghost columns); 0 if invalid. */
+size_t wblbe_batch_case_bytes(const wblbe_params* params);
+
+/* Create a batch on the current device.  dev_workspace: 256-byte aligned,
+ * borrowed until destroy.  EINVAL / ENOMEM (workspace below the control
+ * region) / ECUDA. */
+wblbe_status wblbe_batch_create(int32_t scheme, int32_t precision,
+                                int32_t max_cases, int32_t max_tiles,
+                                int64_t max_case_nodes, void* dev_workspace,
+                                size_t workspace_bytes, void* cuda_stream,
+                                const wblbe_batch_config* config,
+                                wblbe_batch_handle* out);
+wblbe_status wblbe_batch_set_config(wblbe_batch_handle b,
+                                    const wblbe_batch_config* config);
+wblbe_status wblbe_batch_get_config(wblbe_batch_handle b,
+                                    wblbe_batch_config* config);
+
+/* Spins (about 64 ns each) a tile waits for a neighbour before the launch
+ * gives up with WBLBE_ETIMEOUT (default 2^22).  Small values exist to
+ * exercise that path. */
+wblbe_status wblbe_batch_set_wait_limit(wblbe_batch_handle b, int64_t spins);
+
+/* Admit a case: params (scheme/precision of the batch, nx, ny >= 8),
+ * initial density rho ([ny][nx] float64, host), the max|u| tolerance that
+ * counts as equilibrium and a step budget.  The case starts at rest,
+ * f = f^eq(rho, 0).  ENOMEM when no case slot, arena range or tile-table room
+ * is free: the caller keeps the request queued and retries after a retire. */
+wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
+                               const double* rho, double umax_tol,
+                               int64_t max_steps, int64_t* case_id);
+
+/* Run up to `launches` persistent launches, each advancing every running
+ * case by steps_per_launch steps.  After every launch the statistics of the
+ * running cases (of the state the launch's last step started from) are read
+ * and the cases that converged, reached their step budget (checked at launch
+ * boundaries, so a budget that is not a multiple of steps_per_launch is
+ * overrun by less than one launch) or became unstable stop and leave the
+ * next launch.  Blocking.  ETIMEOUT if a tile wait gave up (the batch state
+ * is then invalid). */
+wblbe_status wblbe_batch_advance(wblbe_batch_handle b, int32_t launches);
+
+/* Ids of cases that stopped since the last poll (at most cap). */
+wblbe_status wblbe_batch_poll(wblbe_batch_handle b, int64_t* ids, int32_t cap,
+                              int32_t* n_done);
+wblbe_status wblbe_batch_case_info(wblbe_batch_handle b, int64_t case_id,
+                                   wblbe_case_info* info);
+
+/* Macroscopic fields ([ny][nx] float64 host arrays, any may be NULL) and
+ * stats of a resident case; populations f_i(x, t) as [9][ny][nx] float64. */
+wblbe_status wblbe_batch_fetch(wblbe_batch_handle b, int64_t case_id,
+                               double* rho, double* ux, double* uy, double* mu,
+                               wblbe_stats* stats);
+wblbe_status wblbe_batch_get_populations(wblbe_batch_handle b, int64_t case_id,
+                                         double* f);
+
+/* Free a case's slot, arena range and tiles. */
+wblbe_status wblbe_batch_retire(wblbe_batch_handle b, int64_t case_id);
+
+/* Cases resident and running, tiles of the running cases, free arena bytes
+ * (any pointer may be NULL). */
+wblbe_status wblbe_batch_counts(wblbe_batch_handle b, int32_t* resident,
+                                int32_t* running, int32_t* tiles,
+                                size_t* arena_free);
+int64_t wblbe_batch_kernel_launches(wblbe_batch_handle b);
+wblbe_status wblbe_batch_destroy(wblbe_batch_handle b);
+const char* wblbe_batch_last_error(wblbe_batch_handle b);
+
 /* ---- allocation-free statistics pass ------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
  * cannot allocate device memory at all: code running while a CUDA graph is

@@ -15,7 +15,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 LIB_DIR = PKG / "_lib"
 LIB_PATH = LIB_DIR / f"libwblbe_{platform.machine()}.so"
-SOURCES = [CSRC / "wblbe.cu", CSRC / "wblbe_noalloc.cu"]
+SOURCES = [CSRC / "wblbe.cu", CSRC / "batch.cu", CSRC / "wblbe_noalloc.cu"]
 DEPENDS = SOURCES + [CSRC / "lbm_kernels.cuh", ROOT / "include" / "wblbe.h"]
 
 NVCC_FLAGS = [

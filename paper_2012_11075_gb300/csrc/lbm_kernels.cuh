@@ -320,10 +320,28 @@ __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size
 // offset is a compile-time constant.
 // blockDim.x = TX; grid = (ceil(nx / TX), ceil(ny / rows)).
 // Dynamic shared memory: strip_smem_bytes(TX, kStages, sizeof(T)).
-template <typename T, bool WB, bool MOMENTS, int TX>
-__global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
-    lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
-                     const KParams p, const MomentsOut mo) {
+// What one strip pass does with each collided row.
+enum StripMode {
+  kModeStep = 0,       // store the post-collision populations
+  kModeMoments = 1,    // write rho, u, mu fields and per-CTA stats, no store
+  kModeStepStats = 2   // store, and accumulate per-CTA stats of f(t)
+};
+
+// GHOST selects the row layout with ghost columns used by the batched
+// kernel: column x of a row is stored at x + 4 and the four columns on each
+// side hold copies of the wrapped columns (x = -4..-1 -> nx-4..nx-1,
+// x = nx..nx+3 -> 0..3), refreshed by every store of a boundary column.  A
+// strip then reads one contiguous range per plane row, always in 16-byte
+// chunks through L2 (cp.async.cg), whatever its width: needed when one
+// kernel launch reads data that other CTAs wrote during the same launch (L1
+// is not coherent across SMs).  Requires nx >= 8 and pitch >= nx + 12.
+template <typename T, bool WB, int MODE, int TX, bool GHOST = false>
+__device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restrict__ dst,
+                                           const KParams& p, const MomentsOut& mo, int x0,
+                                           int y0, int y1, double* stats_rec,
+                                           unsigned char* smem_raw) {
+  constexpr bool MOMENTS = MODE == kModeMoments;
+  constexpr bool STATS = MODE != kModeStep;
   constexpr int R = Staging<T>::kRows;     // rows per iteration
   constexpr int PDG = Staging<T>::kAhead;  // row groups requested ahead of use
   constexpr int kStages = Staging<T>::kStages;
@@ -331,7 +349,6 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   constexpr int E = 16 / sizeof(T);        // elements per 16-byte chunk
   constexpr int NCH = SW / E;              // chunks per plane row
   constexpr int kMaxChunks = (9 * NCH + TX - 1) / TX;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   // 128-byte aligned base (16-byte copies need 16)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
@@ -340,11 +357,9 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   T* mu_s = rho_s + kRing * SW;                        // [kMuRing][SW]
 
   const int tx = threadIdx.x;
-  const int x0 = blockIdx.x * TX;
   const int w = min(TX, p.nx - x0);        // valid columns of this strip
-  const int y0 = blockIdx.y * p.rows;
-  const int y1 = min(y0 + p.rows, p.ny);
   const bool own = tx < w;
+  __syncthreads();                         // a previous pass may still read smem
   const int sx = tx + kPad;                // slot of the own column
   // Halo work, kept in warp 0 (threads 0-3 take the densities of slots 2, 3
   // (x0-2, x0-1) and w+4, w+5 (x0+w, x0+w+1); threads 0 and 1 take mu at
@@ -352,7 +367,11 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   const bool halo = tx < 4;
   const int hs = tx < 2 ? 2 + tx : w + 2 + tx;
   const int mu_lo = 0, mu_hi = 1;
-  const bool use_vec = (w == TX) && (p.nx % 4 == 0);
+  const bool use_vec = GHOST || ((w == TX) && (p.nx % 4 == 0));
+  // 16-byte chunks per plane row this strip needs (its columns plus 4 on
+  // each side, rounded up to whole chunks; never past the stage row)
+  const int nch_rt = GHOST ? (w + 2 * kPad + (16 / (int)sizeof(T)) - 1) / (16 / (int)sizeof(T))
+                           : (TX + 2 * kPad) / (16 / (int)sizeof(T));
 
   const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa6 = T(p.kappa / 6.0);
   const CollideConsts<T> cc(p);
@@ -367,11 +386,15 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
 #pragma unroll
   for (int c = 0; c < kMaxChunks; ++c) {
     const int q = tx + c * TX;
-    ch_on[c] = use_vec && q < 9 * NCH;
-    const int i = ch_on[c] ? q / NCH : 0, j = ch_on[c] ? q - i * NCH : 0;
+    ch_on[c] = use_vec && q < 9 * nch_rt;
+    const int i = ch_on[c] ? q / nch_rt : 0, j = ch_on[c] ? q - i * nch_rt : 0;
     int col = x0 - kPad + j * E;
-    if (col < 0) col += p.nx;
-    else if (col >= p.nx) col -= p.nx;
+    if (GHOST) {
+      col += kPad;                         // storage offset of column x is x + 4
+    } else {
+      if (col < 0) col += p.nx;
+      else if (col >= p.nx) col -= p.nx;
+    }
     ch_src[c] = src + i * p.plane + col;
     ch_dst[c] = i * SW + j * E;
     ch_dy[c] = dir_cy(i);
@@ -442,7 +465,12 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   auto wrap_slot = [](int sl) { return sl >= kStages ? sl - kStages : sl; };
 
   // running output positions of the next row to collide
-  T* out_row = dst + (long long)y0 * p.pitch + x0 + tx;
+  T* out_row = dst + (long long)y0 * p.pitch + x0 + tx + (GHOST ? kPad : 0);
+  // ghost copies a boundary column also writes (storage offsets relative to
+  // its own): x < 4 -> +nx (right ghost), x >= nx - 4 -> -nx (left ghost)
+  const int xg = x0 + tx;
+  const bool ghost_r = GHOST && own && xg < kPad;
+  const bool ghost_l = GHOST && own && xg >= p.nx - kPad;
   long long mom_row = (long long)y0 * p.nx + x0 + tx;
 
   int sq = 0;                              // stage slot of the next requested row
@@ -510,17 +538,22 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
             *out = g[i];
+            if (ghost_r) out[p.nx] = g[i];
+            if (ghost_l) out[-p.nx] = g[i];
             out += p.plane;
           }
-        } else {
+        }
+        if (STATS) {
           const double rho = (double)rs + p.rho_ref;
           const double mu = (double)m_c[sx];
           const double dux = (double)ux, duy = (double)uy;
-          const long long kk = mom_row + (long long)j * p.nx;
-          if (mo.rho) mo.rho[kk] = rho;
-          if (mo.ux) mo.ux[kk] = dux;
-          if (mo.uy) mo.uy[kk] = duy;
-          if (mo.mu) mo.mu[kk] = mu;
+          if (MOMENTS) {
+            const long long kk = mom_row + (long long)j * p.nx;
+            if (mo.rho) mo.rho[kk] = rho;
+            if (mo.ux) mo.ux[kk] = dux;
+            if (mo.uy) mo.uy[kk] = duy;
+            if (mo.mu) mo.mu[kk] = mu;
+          }
           const double u2 = dux * dux + duy * duy;
           st_mass += rho;
           st_kin += 0.5 * rho * u2;
@@ -543,7 +576,7 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   }
   cp_async_wait<0>();
 
-  if (MOMENTS && mo.partials) {
+  if (STATS && stats_rec) {
     // deterministic block reduction: warp shuffle, then thread 0 over warps
     __shared__ double red[kMaxTile / 32][kStatRec];
     double v[kStatRec] = {st_mass, st_kin, st_u2, st_mumin, st_mumax, (double)st_bad};
@@ -579,11 +612,27 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
         r[4] = fmax(r[4], red[q][4]);
         r[5] = fmax(r[5], red[q][5]);
       }
-      double* out = mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec;
 #pragma unroll
-      for (int q = 0; q < kStatRec; ++q) out[q] = r[q];
+      for (int q = 0; q < kStatRec; ++q) stats_rec[q] = r[q];
     }
   }
+}
+
+// One CTA per strip segment: blockIdx.x picks the strip, blockIdx.y the run
+// of p.rows rows.  Moments mode writes the per-CTA stats record.
+template <typename T, bool WB, bool MOMENTS, int TX>
+__global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
+    lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                     const KParams p, const MomentsOut mo) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * p.rows;
+  const int y1 = min(y0 + p.rows, p.ny);
+  double* rec = (MOMENTS && mo.partials)
+                    ? mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec
+                    : nullptr;
+  strip_pass<T, WB, MOMENTS ? kModeMoments : kModeStep, TX>(src, dst, p, mo, x0, y0, y1, rec,
+                                                              smem_raw);
 }
 
 // Final reduction of the per-CTA records, one block, fixed order.

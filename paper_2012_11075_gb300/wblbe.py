@@ -53,6 +53,19 @@ class CLaunch(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("rows_per_cta", ctypes.c_int32)]
 
 
+class CBatchConfig(ctypes.Structure):
+    _fields_ = [("tile_x", ctypes.c_int32), ("rows_per_tile", ctypes.c_int32),
+                ("steps_per_launch", ctypes.c_int32)]
+
+
+class CCaseInfo(ctypes.Structure):
+    _fields_ = [("case_id", ctypes.c_int64), ("state", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("stats", CStats)]
+
+
+CASE_RUNNING, CASE_CONVERGED, CASE_MAXSTEPS, CASE_UNSTABLE = range(4)
+
+
 # Every entry point declared in include/wblbe.h with its ctypes signature.
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
@@ -77,6 +90,32 @@ _SIGNATURES = {
     "wblbe_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_destroy": (ctypes.c_int, [_H]),
     "wblbe_last_error": (ctypes.c_char_p, [_H]),
+    "wblbe_batch_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32,
+                                                      ctypes.c_int64, ctypes.c_size_t]),
+    "wblbe_batch_case_bytes": (ctypes.c_size_t, [ctypes.POINTER(CParams)]),
+    "wblbe_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_size_t,
+                                          _P, ctypes.POINTER(CBatchConfig), ctypes.POINTER(_H)]),
+    "wblbe_batch_set_config": (ctypes.c_int, [_H, ctypes.POINTER(CBatchConfig)]),
+    "wblbe_batch_get_config": (ctypes.c_int, [_H, ctypes.POINTER(CBatchConfig)]),
+    "wblbe_batch_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "wblbe_batch_admit": (ctypes.c_int, [_H, ctypes.POINTER(CParams), _P, ctypes.c_double,
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
+    "wblbe_batch_advance": (ctypes.c_int, [_H, ctypes.c_int32]),
+    "wblbe_batch_poll": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "wblbe_batch_case_info": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.POINTER(CCaseInfo)]),
+    "wblbe_batch_fetch": (ctypes.c_int, [_H, ctypes.c_int64, _P, _P, _P, _P,
+                                         ctypes.POINTER(CStats)]),
+    "wblbe_batch_get_populations": (ctypes.c_int, [_H, ctypes.c_int64, _P]),
+    "wblbe_batch_retire": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "wblbe_batch_counts": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_size_t)]),
+    "wblbe_batch_kernel_launches": (ctypes.c_int64, [_H]),
+    "wblbe_batch_destroy": (ctypes.c_int, [_H]),
+    "wblbe_batch_last_error": (ctypes.c_char_p, [_H]),
     "wblbe_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(CParams), _P, _P, _P, _P, _P,
                                              ctypes.POINTER(CStats), _P]),
     "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
@@ -268,3 +307,125 @@ class Solver:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.wblbe_kernel_launches(self.h))
+
+
+class Batch:
+    """Many independent cases resident on the device, advanced together by
+    the persistent batched kernel (C ABI wblbe_batch_*).
+
+    ``arena_bytes`` of device memory hold the cases' populations; admission
+    returns None (the caller queues the request) when no slot, arena range
+    or tile-table room is free."""
+
+    def __init__(self, scheme=WELL_BALANCED, precision=FP32_SHIFTED, max_cases=64,
+                 max_tiles=1 << 15, max_case_nodes=1 << 20, arena_bytes=1 << 30,
+                 tile_x=128, rows_per_tile=32, steps_per_launch=1, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise RuntimeError("wblbe needs a CUDA device")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        nbytes = int(self.lib.wblbe_batch_workspace_bytes(max_cases, max_tiles, max_case_nodes,
+                                                          arena_bytes))
+        if nbytes == 0:
+            raise WblbeError(EINVAL, "invalid batch sizes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        cfg = CBatchConfig(tile_x, rows_per_tile, steps_per_launch)
+        h = ctypes.c_void_p()
+        st = self.lib.wblbe_batch_create(scheme, precision, max_cases, max_tiles, max_case_nodes,
+                                         ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                         ctypes.c_void_p(self.stream.cuda_stream),
+                                         ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise WblbeError(st, self.lib.wblbe_batch_last_error(None).decode())
+        self.h = h
+        self.scheme, self.precision = scheme, precision
+
+    def _check(self, st, allow=(OK,)):
+        if st not in allow:
+            raise WblbeError(st, self.lib.wblbe_batch_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._check(self.lib.wblbe_batch_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_config(self, tile_x, rows_per_tile, steps_per_launch):
+        cfg = CBatchConfig(tile_x, rows_per_tile, steps_per_launch)
+        self._check(self.lib.wblbe_batch_set_config(self.h, ctypes.byref(cfg)))
+
+    def get_config(self):
+        cfg = CBatchConfig()
+        self._check(self.lib.wblbe_batch_get_config(self.h, ctypes.byref(cfg)))
+        return cfg.tile_x, cfg.rows_per_tile, cfg.steps_per_launch
+
+    def set_wait_limit(self, spins):
+        self._check(self.lib.wblbe_batch_set_wait_limit(self.h, int(spins)))
+
+    def case_bytes(self, params: Params) -> int:
+        cp = params.c()
+        return int(self.lib.wblbe_batch_case_bytes(ctypes.byref(cp)))
+
+    def admit(self, params: Params, rho, umax_tol: float, max_steps: int):
+        """Returns the case id, or None when the batch is full (ENOMEM)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        assert rho.shape == (params.ny, params.nx)
+        cp = params.c()
+        cid = ctypes.c_int64()
+        st = self._check(self.lib.wblbe_batch_admit(self.h, ctypes.byref(cp),
+                                                    ctypes.c_void_p(rho.ctypes.data),
+                                                    float(umax_tol), int(max_steps),
+                                                    ctypes.byref(cid)), allow=(OK, ENOMEM))
+        return None if st == ENOMEM else int(cid.value)
+
+    def advance(self, launches: int = 1):
+        self._check(self.lib.wblbe_batch_advance(self.h, int(launches)))
+
+    def poll(self, cap: int = 4096):
+        ids = (ctypes.c_int64 * cap)()
+        n = ctypes.c_int32()
+        self._check(self.lib.wblbe_batch_poll(self.h, ids, cap, ctypes.byref(n)))
+        return [int(ids[k]) for k in range(n.value)]
+
+    def info(self, case_id: int) -> dict:
+        ci = CCaseInfo()
+        self._check(self.lib.wblbe_batch_case_info(self.h, int(case_id), ctypes.byref(ci)))
+        return {"case_id": ci.case_id, "state": ci.state, "steps": ci.steps,
+                "stats": ci.stats.as_dict()}
+
+    def fetch(self, case_id: int, shape):
+        outs = [np.empty(shape) for _ in range(4)]
+        st = CStats()
+        self._check(self.lib.wblbe_batch_fetch(self.h, int(case_id),
+                                               *[ctypes.c_void_p(o.ctypes.data) for o in outs],
+                                               ctypes.byref(st)))
+        return dict(zip(("rho", "ux", "uy", "mu"), outs)), st.as_dict()
+
+    def get_populations(self, case_id: int, shape) -> np.ndarray:
+        f = np.empty((9,) + tuple(shape))
+        self._check(self.lib.wblbe_batch_get_populations(self.h, int(case_id),
+                                                         ctypes.c_void_p(f.ctypes.data)))
+        return f
+
+    def retire(self, case_id: int):
+        self._check(self.lib.wblbe_batch_retire(self.h, int(case_id)))
+
+    def counts(self) -> dict:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        fr = ctypes.c_size_t()
+        self._check(self.lib.wblbe_batch_counts(self.h, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c), ctypes.byref(fr)))
+        return {"resident": a.value, "running": b.value, "tiles": c.value,
+                "arena_free": fr.value}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.wblbe_batch_kernel_launches(self.h))
