@@ -230,6 +230,102 @@ def time_e2e(solver, rho_pinned, rho_out_pinned, substeps, steps, warmup, torch)
     return time.perf_counter() - t0
 
 
+def run_batched(args, stream, torch):
+    """The uneven batched case mix: 512 independent cases (sides 64..512
+    log-uniform, flat/droplet, ratio 2..50, tau 0.55..1.2), FP32-shifted
+    state with FP64 reductions, 5000 steps each, one persistent launch per
+    steps_per_launch steps, the launch configuration chosen by the
+    autotuner on a 64-case subsample.  Latency of a case = time from the
+    start of the solve to the launch after which it stopped."""
+    from paper_2012_11075_gb300 import autotune, wblbe
+    from paper_2012_11075_gb300 import workloads as wl
+    specs = wl.batched_case_specs(count=args.batch_cases, seed=4)
+    gpu = torch.cuda.get_device_name()
+
+    def params(sp):
+        return wblbe.Params(sp["nx"], sp["ny"], sp["tau"], sp["kappa"], sp["beta"], sp["rho_l"],
+                            sp["rho_g"], scheme=wblbe.WELL_BALANCED,
+                            precision=wblbe.FP32_SHIFTED)
+
+    probe = wblbe.Batch(max_cases=1, arena_bytes=1 << 20, stream=stream)
+    case_bytes = [probe.case_bytes(params(sp)) for sp in specs]
+    probe.close()
+    sub = specs[:64]
+    tb = wblbe.Batch(max_cases=len(sub), max_tiles=1 << 16, max_case_nodes=512 * 512,
+                     arena_bytes=int(sum(case_bytes[:64]) * 1.02) + (1 << 20), stream=stream)
+    for sp in sub:
+        tb.admit(params(sp), wl.case_field(sp), 0.0, 10 ** 9)
+    tuned = autotune.tune(tb, [(sp["nx"], sp["ny"]) for sp in sub], gpu, launches=2,
+                          sync=torch.cuda.synchronize)
+    tb.close()
+    cfg = tuned["config"]
+    b = wblbe.Batch(max_cases=len(specs), max_tiles=1 << 18, max_case_nodes=512 * 512,
+                    arena_bytes=int(sum(case_bytes) * 1.02) + (1 << 20), tile_x=cfg[0],
+                    rows_per_tile=cfg[1], steps_per_launch=cfg[2], stream=stream)
+    fields = [wl.case_field(sp) for sp in specs]
+    t0 = time.perf_counter()
+    ids = [b.admit(params(sp), f, 0.0, args.batch_steps) for sp, f in zip(specs, fields)]
+    torch.cuda.synchronize()
+    t_admit = time.perf_counter() - t0
+    assert None not in ids
+    nodes = {cid: sp["nx"] * sp["ny"] for cid, sp in zip(ids, specs)}
+    done_at = {}
+    l0 = b.kernel_launches
+    t0 = time.perf_counter()
+    while b.counts()["running"] > 0:
+        b.advance(1)
+        t = time.perf_counter() - t0
+        for cid in b.poll():
+            done_at[cid] = t
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    infos = {cid: b.info(cid) for cid in ids}
+    node_steps = sum(nodes[cid] * infos[cid]["steps"] for cid in ids)
+    states = {}
+    for cid in ids:
+        states[str(infos[cid]["state"])] = states.get(str(infos[cid]["state"]), 0) + 1
+    lat = np.array([done_at.get(cid, t_solve) for cid in ids])
+    launches = b.kernel_launches - l0
+    b.close()
+    return {"workload": f"batched_{len(specs)}_uneven_cases_wb_fp32",
+            "cases": len(specs), "nodes": int(sum(nodes.values())),
+            "steps_per_case": args.batch_steps, "config": cfg,
+            "tuned_from_cache": tuned.get("cached", False), "tuning_mlups": tuned.get("candidates"),
+            "admit_s": t_admit, "solve_s": t_solve, "mlups": node_steps / t_solve / 1e6,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "states": states, "state_names": {"1": "converged", "2": "budget", "3": "unstable"},
+            "gpu_launches": int(launches)}
+
+
+def run_serving(args, stream, torch, cfg):
+    """Continuous batching of relax-to-equilibrium requests arriving as a
+    Poisson process (sides 32..1024 log-uniform, case parameters as the
+    batched mix), each run to max|u| < 1e-6 (FP32) / 1e-10 (FP64) or 200000
+    steps, for a fixed window per arrival rate; requests are admitted as
+    slots and memory free up."""
+    from paper_2012_11075_gb300 import serve, wblbe
+    out = {}
+    for name, prec in (("fp32", wblbe.FP32_SHIFTED), ("fp64", wblbe.FP64)):
+        out[name] = {}
+        for rate in args.serve_rates:
+            reqs = serve.make_requests(rate, args.serve_window, seed=5, precision=prec,
+                                       scheme=wblbe.WELL_BALANCED)
+            b = wblbe.Batch(precision=prec, max_cases=256, max_tiles=1 << 17,
+                            max_case_nodes=1024 * 1024, arena_bytes=args.serve_arena_gb << 30,
+                            tile_x=cfg[0], rows_per_tile=cfg[1], steps_per_launch=cfg[2],
+                            stream=stream)
+            srv = serve.Server(b)
+            rep = srv.run(reqs, duration=args.serve_window, drain=False)
+            b.close()
+            out[name][str(rate)] = rep.summary()
+    return {"workload": "poisson_relax_to_equilibrium_wb", "window_s": args.serve_window,
+            "policy": "admit by slot and arena room, one launch per loop, stop at launch "
+                      "boundaries, fixed window (requests still queued or running at the "
+                      "end are reported, not counted as completed)",
+            "results": out}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2012_11075_gb300 import wblbe
@@ -328,6 +424,10 @@ def run_ours(args, world, rank, local):
                    "f64_umax": r64["umax"], "f64_mass_drift_rel": r64["mass_drift"],
                    "nonfinite": bool(r32["nonfinite"] or r64["nonfinite"])},
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, stream, torch)
+        if not args.no_serving:
+            line["serving"] = run_serving(args, stream, torch, line["batched"]["config"])
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(pr)
     print(json.dumps(line), flush=True)
@@ -345,6 +445,13 @@ def main():
                     help="lattice side (4096 is the benchmark; smaller sides are for profiling)")
     ap.add_argument("--only", choices=["both", "f32", "f64"], default="both")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-cases", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--serve-window", type=float, default=5.0)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[50.0, 200.0, 1000.0])
+    ap.add_argument("--serve-arena-gb", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -280,6 +280,8 @@ struct wblbe_batch {
     double mass0 = 0.0;
     wblbe_stats last{};
     int64_t id = -1;
+    std::vector<TileDev> tiles;            // local tiles, nb = local indices
+    int tiles_tx = 0, tiles_rows = 0;      // configuration they were cut for
   };
   std::vector<Case> cases;
   int64_t next_id = 0;
@@ -410,14 +412,13 @@ LayoutParams case_layout(const wblbe_batch::Case& c) {
   return lp;
 }
 
-// Does the periodic interval [a - h, b + h) (mod n) meet [c, d)?
+// Does the periodic interval [a - h, b + h) (mod n) meet [c, d) (0 <= c < d <= n)?
 bool periodic_meet(int a, int b, int c, int d, int h, int n) {
-  if ((b - a) + 2 * h >= n) return true;
-  for (int x = c; x < d; ++x) {
-    int r = ((x - (a - h)) % n + n) % n;
-    if (r < (b - a) + 2 * h) return true;
-  }
-  return false;
+  const int len = (b - a) + 2 * h;
+  if (len >= n) return true;
+  const int s = (((a - h) % n) + n) % n;
+  if (s + len <= n) return std::max(s, c) < std::min(s + len, d);
+  return std::max(s, c) < d || c < s + len - n;     // [s, n) and [0, s + len - n)
 }
 
 // Tiles of a case: strips of tile_x columns (x0 a multiple of tile_x) and
@@ -440,43 +441,76 @@ void case_tiles(const wblbe_batch::Case& c, int case_idx, const wblbe_batch_conf
   }
 }
 
+// Cut a case into tiles for the current configuration and find, for every
+// tile, the tiles of the same case its halo reads (local indices).  Cached
+// until the configuration changes.
+wblbe_status ensure_case_tiles(wblbe_batch* b, wblbe_batch::Case& c) {
+  if (c.tiles_tx == b->cfg.tile_x && c.tiles_rows == b->cfg.rows_per_tile && !c.tiles.empty())
+    return WBLBE_OK;
+  c.tiles.clear();
+  case_tiles(c, 0, b->cfg, c.tiles);
+  const int nt = (int)c.tiles.size();
+  for (int a = 0; a < nt; ++a) {
+    TileDev& ta = c.tiles[a];
+    const int wa = std::min(b->cfg.tile_x, c.p.nx - ta.x0);
+    int n = 0;
+    for (int q = 0; q < nt; ++q) {
+      if (q == a) continue;
+      const TileDev& tq = c.tiles[q];
+      const int wq = std::min(b->cfg.tile_x, c.p.nx - tq.x0);
+      if (periodic_meet(ta.x0, ta.x0 + wa, tq.x0, tq.x0 + wq, kHaloReach, c.p.nx) &&
+          periodic_meet(ta.y0, ta.y1, tq.y0, tq.y1, kHaloReach, c.p.ny)) {
+        if (n == kMaxNb) {
+          c.tiles.clear();
+          return bfail(b, WBLBE_EINVAL, "a tile of case %lld has more than %d neighbours; "
+                       "use larger tiles", (long long)c.id, kMaxNb);
+        }
+        ta.nb[n++] = q;
+      }
+    }
+  }
+  c.tiles_tx = b->cfg.tile_x;
+  c.tiles_rows = b->cfg.rows_per_tile;
+  return WBLBE_OK;
+}
+
+wblbe_status upload_case_entry(wblbe_batch* b, int ci) {
+  const auto& c = b->cases[ci];
+  CaseDev cd{};
+  cd.kp = case_kparams(c, b->cfg.rows_per_tile);
+  cd.off[0] = (long long)(c.off / b->elem);
+  cd.off[1] = (long long)((c.off + c.bytes / 2) / b->elem);
+  cd.cur = c.cur;
+  BCU(b, cudaMemcpyAsync(b->d_cases + ci, &cd, sizeof(cd), cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));    // cd lives on this stack frame
+  return WBLBE_OK;
+}
+
+// Concatenate the running cases' tiles (global neighbour indices) and upload
+// the tile table and the running-case list.
 wblbe_status rebuild_tiles(wblbe_batch* b) {
   std::vector<TileDev> tiles;
   b->run_host.clear();
   for (size_t ci = 0; ci < b->cases.size(); ++ci) {
-    const auto& c = b->cases[ci];
+    auto& c = b->cases[ci];
     if (!c.used || !c.running) continue;
+    wblbe_status st = ensure_case_tiles(b, c);
+    if (st != WBLBE_OK) return st;
     RunCase rc{};
     rc.c = (int)ci;
     rc.t0 = (int)tiles.size();
-    case_tiles(c, (int)ci, b->cfg, tiles);
-    rc.nt = (int)tiles.size() - rc.t0;
+    rc.nt = (int)c.tiles.size();
+    for (TileDev t : c.tiles) {
+      t.c = (int)ci;
+      for (int q = 0; q < kMaxNb; ++q)
+        if (t.nb[q] >= 0) t.nb[q] += rc.t0;
+      tiles.push_back(t);
+    }
     b->run_host.push_back(rc);
   }
   if ((int)tiles.size() > b->max_tiles)
     return bfail(b, WBLBE_ENOMEM, "running cases need %zu tiles, the batch holds %d", tiles.size(),
                  b->max_tiles);
-  // neighbours: tiles of the same case whose data the tile's halo reads
-  for (const RunCase& rc : b->run_host) {
-    const auto& c = b->cases[rc.c];
-    for (int a = rc.t0; a < rc.t0 + rc.nt; ++a) {
-      TileDev& ta = tiles[a];
-      const int wa = std::min(b->cfg.tile_x, c.p.nx - ta.x0);
-      int n = 0;
-      for (int q = rc.t0; q < rc.t0 + rc.nt; ++q) {
-        if (q == a) continue;
-        const TileDev& tq = tiles[q];
-        const int wq = std::min(b->cfg.tile_x, c.p.nx - tq.x0);
-        if (periodic_meet(ta.x0, ta.x0 + wa, tq.x0, tq.x0 + wq, kHaloReach, c.p.nx) &&
-            periodic_meet(ta.y0, ta.y1, tq.y0, tq.y1, kHaloReach, c.p.ny)) {
-          if (n == kMaxNb)
-            return bfail(b, WBLBE_EINVAL, "a tile of case %lld has more than %d neighbours; "
-                         "use larger tiles", (long long)c.id, kMaxNb);
-          ta.nb[n++] = q;
-        }
-      }
-    }
-  }
   b->ntiles = (int)tiles.size();
   b->nrun = (int)b->run_host.size();
   if (!tiles.empty())
@@ -485,7 +519,7 @@ wblbe_status rebuild_tiles(wblbe_batch* b) {
   if (!b->run_host.empty())
     BCU(b, cudaMemcpyAsync(b->d_run, b->run_host.data(), b->run_host.size() * sizeof(RunCase),
                            cudaMemcpyHostToDevice, b->stream));
-  // case table (rows per tile enters KParams for the moments pass)
+  // the case table carries rows_per_tile (moments) and the buffer parity
   for (size_t ci = 0; ci < b->cases.size(); ++ci) {
     const auto& c = b->cases[ci];
     if (!c.used) continue;
@@ -798,32 +832,33 @@ wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
   for (int i = 0; i < b->max_cases; ++i)
     if (!b->cases[i].used) { slot = i; break; }
   if (slot < 0) return bfail(b, WBLBE_ENOMEM, "no free case slot (%d in use)", b->max_cases);
-  // tiles this case adds
+  // tiles this case adds (running cases' tile lists are cached per config)
+  wblbe_batch::Case& c = b->cases[slot];
+  c = wblbe_batch::Case();
+  c.p = *params;
+  c.id = b->next_id;
   {
-    int ntiles = b->ntiles;
-    if (b->tiles_dirty) {
-      ntiles = 0;
-      for (const auto& c : b->cases) {
-        if (!c.used || !c.running) continue;
-        std::vector<TileDev> tmp;
-        case_tiles(c, 0, b->cfg, tmp);
-        ntiles += (int)tmp.size();
-      }
+    wblbe_status st = ensure_case_tiles(b, c);
+    if (st != WBLBE_OK) { c = wblbe_batch::Case(); return st; }
+    long long ntiles = (long long)c.tiles.size();
+    for (size_t ci = 0; ci < b->cases.size(); ++ci) {
+      auto& o = b->cases[ci];
+      if ((int)ci == slot || !o.used || !o.running) continue;
+      st = ensure_case_tiles(b, o);
+      if (st != WBLBE_OK) { c = wblbe_batch::Case(); return st; }
+      ntiles += (long long)o.tiles.size();
     }
-    wblbe_batch::Case probe;
-    probe.p = *params;
-    std::vector<TileDev> tmp;
-    case_tiles(probe, 0, b->cfg, tmp);
-    if (ntiles + (int)tmp.size() > b->max_tiles)
-      return bfail(b, WBLBE_ENOMEM, "tile table full (%d + %zu > %d)", ntiles, tmp.size(),
-                   b->max_tiles);
+    if (ntiles > b->max_tiles) {
+      c = wblbe_batch::Case();
+      return bfail(b, WBLBE_ENOMEM, "tile table full (%lld > %d)", ntiles, b->max_tiles);
+    }
   }
   const size_t bytes = case_bytes(params, b->elem);
   size_t off = 0;
-  if (!alloc_range(b, bytes, &off))
+  if (!alloc_range(b, bytes, &off)) {
+    c = wblbe_batch::Case();
     return bfail(b, WBLBE_ENOMEM, "arena has no free range of %zu bytes", bytes);
-  wblbe_batch::Case& c = b->cases[slot];
-  c = wblbe_batch::Case();
+  }
   c.used = true;
   c.running = true;
   c.reported = false;
@@ -835,7 +870,7 @@ wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
   c.bytes = bytes;
   c.tol = umax_tol;
   c.max_steps = max_steps;
-  c.id = b->next_id++;
+  b->next_id++;
   // initial state
   const size_t nodes = (size_t)params->nx * params->ny;
   BCU(b, cudaMemcpyAsync(b->d_stage, rho, nodes * sizeof(double), cudaMemcpyHostToDevice, b->stream));
@@ -851,8 +886,8 @@ wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
         b->d_stage, reinterpret_cast<float*>(b->arena + c.off), params->nx, params->ny, c.pitch,
         c.plane, wb, params->rho0, lp);
   BCU(b, cudaGetLastError());
-  b->tiles_dirty = true;
-  wblbe_status st = rebuild_tiles(b);     // also writes this case's table entry
+  b->tiles_dirty = true;                  // the tile table is rebuilt before the next launch
+  wblbe_status st = upload_case_entry(b, slot);
   if (st != WBLBE_OK) return st;
   st = case_moments(b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
   if (st != WBLBE_OK) return st;
@@ -1024,14 +1059,12 @@ wblbe_status wblbe_batch_counts(wblbe_batch_handle b, int32_t* resident, int32_t
                                 int32_t* tiles, size_t* arena_free) {
   if (!b) return bfail(nullptr, WBLBE_EINVAL, "handle is NULL");
   int res = 0, run = 0, nt = 0;
-  for (const auto& c : b->cases) {
+  for (auto& c : b->cases) {
     if (!c.used) continue;
     ++res;
     if (c.running) {
       ++run;
-      std::vector<TileDev> tmp;
-      case_tiles(c, 0, b->cfg, tmp);
-      nt += (int)tmp.size();
+      if (ensure_case_tiles(b, c) == WBLBE_OK) nt += (int)c.tiles.size();
     }
   }
   size_t fr = 0;

@@ -1,0 +1,182 @@
+"""Continuous-batching serving loop for relax-to-equilibrium requests.
+
+Requests (a case: lattice, parameters, initial density, tolerance, step
+budget) arrive over time.  The loop admits waiting requests into the
+resident batch in arrival order whenever a case slot, arena range and tile
+room are free, advances every resident running case together one persistent
+launch at a time, and retires each case as soon as it stops (converged,
+budget reached or unstable), which frees its memory for the next admission.
+Requests that arrive while others are on the device therefore share launches
+with them.  Latency is completion time minus arrival time.
+
+The batch object is injected (``paper_2012_11075_gb300.wblbe.Batch`` on the
+GPU); the loop itself is host logic and is tested on the CPU with a fake.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float              # seconds since the start of the run
+    params: object              # wblbe.Params
+    rho: object                 # [ny][nx] float64, or a callable building it
+    umax_tol: float
+    max_steps: int
+    admitted: float = math.nan
+    finished: float = math.nan
+    state: int = -1
+    steps: int = 0
+    case_id: int = -1
+
+
+@dataclass
+class ServeReport:
+    completed: list = field(default_factory=list)
+    offered: int = 0
+    admitted: int = 0
+    backlog: int = 0
+    running_at_end: int = 0
+    elapsed: float = 0.0
+    node_steps: float = 0.0
+    launches: int = 0
+
+    def latencies(self):
+        return np.array([r.finished - r.arrival for r in self.completed])
+
+    def summary(self) -> dict:
+        lat = self.latencies()
+        states = collections.Counter(r.state for r in self.completed)
+        return {
+            "offered": self.offered,
+            "admitted": self.admitted,
+            "completed": len(self.completed),
+            "backlog_at_end": self.backlog,
+            "running_at_end": self.running_at_end,
+            "elapsed_s": self.elapsed,
+            "completed_per_s": len(self.completed) / self.elapsed if self.elapsed > 0 else 0.0,
+            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "mlups": self.node_steps / self.elapsed / 1e6 if self.elapsed > 0 else 0.0,
+            "launches": self.launches,
+            "states": {str(k): v for k, v in sorted(states.items())},
+        }
+
+
+class Server:
+    """Admission, advance and retirement around one batch."""
+
+    def __init__(self, batch, clock=time.perf_counter, on_finish=None):
+        self.batch = batch
+        self.clock = clock
+        self.on_finish = on_finish             # called (request, batch) before retirement
+        self.t0 = clock()
+        self.queue = collections.deque()       # waiting requests, arrival order
+        self.resident = {}                     # case_id -> Request
+        self.report = ServeReport()
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, req: Request):
+        self.queue.append(req)
+        self.report.offered += 1
+
+    def admit_waiting(self):
+        """Admit from the head of the queue until the batch refuses."""
+        while self.queue:
+            req = self.queue[0]
+            if callable(req.rho):
+                req.rho = req.rho()            # built when it is first offered
+            cid = self.batch.admit(req.params, req.rho, req.umax_tol, req.max_steps)
+            if cid is None:
+                break                          # full: keep it queued
+            self.queue.popleft()
+            req.case_id = cid
+            req.admitted = self.now()
+            self.resident[cid] = req
+            self.report.admitted += 1
+
+    def step(self):
+        """One launch for every resident running case, then retire finished."""
+        running = [r for r in self.resident.values() if r.state == -1]
+        if not running:
+            return
+        cfg = self.batch.get_config()
+        self.batch.advance(1)
+        self.report.launches += 1
+        self.report.node_steps += cfg[2] * sum(r.params.nx * r.params.ny for r in running)
+        t = self.now()
+        for cid in self.batch.poll():
+            req = self.resident.pop(cid)
+            info = self.batch.info(cid)
+            req.state = info["state"]
+            req.steps = info["steps"]
+            req.finished = t
+            if self.on_finish is not None:
+                self.on_finish(req, self.batch)
+            self.batch.retire(cid)
+            self.report.completed.append(req)
+
+    def run(self, requests, duration: float, drain: bool = False):
+        """Serve ``requests`` (sorted by arrival) in real time until
+        ``duration`` seconds (and, with ``drain``, until all finished)."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        while True:
+            t = self.now()
+            while pending and pending[0].arrival <= t:
+                self.submit(pending.popleft())
+            self.admit_waiting()
+            if self.resident:
+                self.step()
+            elif pending and not self.queue:
+                # idle until the next arrival
+                wait = pending[0].arrival - self.now()
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+            if t >= duration and (not drain or (not pending and not self.queue
+                                                and not self.resident)):
+                break
+        self.report.elapsed = self.now()
+        self.report.backlog = len(self.queue) + len(pending)
+        self.report.running_at_end = len(self.resident)
+        return self.report
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int):
+    """Arrival times of a Poisson process of the given rate on [0, duration)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return out
+        out.append(t)
+
+
+def make_requests(rate: float, duration: float, seed: int, precision: int, scheme: int,
+                  side_min=32, side_max=1024, umax_tol=None, max_steps=200000):
+    """Relax-to-equilibrium requests of the serving workload: sides
+    log-uniform in [side_min, side_max], flat slab or droplet, parameters as
+    the batched case mix; tolerance 1e-6 (FP32) or 1e-10 (FP64)."""
+    import functools
+
+    from . import workloads as wl
+    from .wblbe import FP64, Params
+    times = poisson_arrivals(rate, duration, seed)
+    specs = wl.batched_case_specs(count=len(times), seed=seed + 1, side_min=side_min,
+                                  side_max=side_max)
+    tol = umax_tol if umax_tol is not None else (1e-10 if precision == FP64 else 1e-6)
+    reqs = []
+    for k, (t, sp) in enumerate(zip(times, specs)):
+        p = Params(sp["nx"], sp["ny"], sp["tau"], sp["kappa"], sp["beta"], sp["rho_l"],
+                   sp["rho_g"], scheme=scheme, precision=precision)
+        reqs.append(Request(k, t, p, functools.partial(wl.case_field, sp), tol, max_steps))
+    return reqs

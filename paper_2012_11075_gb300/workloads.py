@@ -148,11 +148,11 @@ def large_domain(n=4096, count=64, ratio=10.0, width=5.0, kappa=0.01, tau=0.7,
                    rho_l, rho_g, rho, name=f"droplets{count}_{n}x{n}_ratio{ratio:g}")
 
 
-def batched_cases(count=512, seed=4, side_min=64, side_max=512):
-    """Uneven independent cases: sides log-uniform in [side_min, side_max]
-    (independently in x and y), flat slab or droplet 50/50, radius/side
-    U[0.1, 0.3], density ratio U[2, 50] with rho_l = 1, tau U[0.55, 1.2],
-    kappa U[0.005, 0.02], W in {3, 4, 5}."""
+def batched_case_specs(count=512, seed=4, side_min=64, side_max=512):
+    """Parameters of uneven independent cases, without their fields: sides
+    log-uniform in [side_min, side_max] (independently in x and y), flat slab
+    or droplet 50/50, radius/side U[0.1, 0.3], density ratio U[2, 50] with
+    rho_l = 1, tau U[0.55, 1.2], kappa U[0.005, 0.02], W in {3, 4, 5}."""
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):
@@ -164,13 +164,30 @@ def batched_cases(count=512, seed=4, side_min=64, side_max=512):
         tau = rng.uniform(0.55, 1.2)
         kappa = rng.uniform(0.005, 0.02)
         width = float(rng.choice([3.0, 4.0, 5.0]))
-        rho_l, rho_g = 1.0, 1.0 / ratio
-        if kind == "flat":
-            prof = slab_profile(ny, rho_l, rho_g, width, ny / 2, frac * ny)
-            rho = np.repeat(prof[:, None], nx, axis=1).copy()
-        else:
-            R = frac * min(nx, ny)
-            rho = droplet_field(nx, ny, [(nx // 2, ny // 2)], [R], rho_l, rho_g, width)
-        out.append(Problem(nx, ny, tau, kappa, beta_for_width(kappa, width, rho_l, rho_g),
-                           rho_l, rho_g, rho, name=f"case{k}_{kind}_{nx}x{ny}"))
+        out.append(dict(k=k, nx=nx, ny=ny, kind=kind, frac=frac, rho_l=1.0, rho_g=1.0 / ratio,
+                        tau=tau, kappa=kappa, width=width,
+                        beta=beta_for_width(kappa, width, 1.0, 1.0 / ratio)))
     return out
+
+
+def case_field(spec) -> np.ndarray:
+    """Initial density of a case spec (flat slab or centred droplet)."""
+    nx, ny = spec["nx"], spec["ny"]
+    if spec["kind"] == "flat":
+        prof = slab_profile(ny, spec["rho_l"], spec["rho_g"], spec["width"], ny / 2,
+                            spec["frac"] * ny)
+        return np.repeat(prof[:, None], nx, axis=1).copy()
+    R = spec["frac"] * min(nx, ny)
+    return droplet_field(nx, ny, [(nx // 2, ny // 2)], [R], spec["rho_l"], spec["rho_g"],
+                         spec["width"])
+
+
+def case_problem(spec) -> Problem:
+    return Problem(spec["nx"], spec["ny"], spec["tau"], spec["kappa"], spec["beta"],
+                   spec["rho_l"], spec["rho_g"], case_field(spec),
+                   name=f"case{spec['k']}_{spec['kind']}_{spec['nx']}x{spec['ny']}")
+
+
+def batched_cases(count=512, seed=4, side_min=64, side_max=512):
+    """The uneven case mix with fields (see batched_case_specs)."""
+    return [case_problem(s) for s in batched_case_specs(count, seed, side_min, side_max)]

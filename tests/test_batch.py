@@ -152,3 +152,38 @@ def test_wait_limit_timeout_is_reported_and_context_survives():
     b.advance(2)
     assert b.info(cid)["state"] == wblbe.CASE_RUNNING
     b.close()
+
+
+def test_serving_results_equal_alone_and_in_the_mix():
+    """Requests served together (arriving while others run, admitted as room
+    frees up) end in exactly the state each reaches when served alone."""
+    from paper_2012_11075_gb300 import serve
+    reqs = serve.make_requests(rate=400.0, duration=0.05, seed=21, precision=wblbe.FP32_SHIFTED,
+                               scheme=wblbe.WELL_BALANCED, side_min=32, side_max=160,
+                               umax_tol=1e-4, max_steps=400)
+    assert len(reqs) >= 8
+    got = {}
+
+    def keep(req, batch):
+        got[req.rid] = (batch.get_populations(req.case_id, (req.params.ny, req.params.nx)),
+                        req.steps, req.state)
+
+    b = wblbe.Batch(max_cases=4, arena_bytes=1 << 26, max_case_nodes=160 * 160, tile_x=64,
+                    rows_per_tile=16, steps_per_launch=8)
+    srv = serve.Server(b, on_finish=keep)
+    rep = srv.run(reqs, duration=0.0, drain=True)
+    b.close()
+    assert len(rep.completed) == len(reqs) and rep.summary()["p99_latency_s"] > 0
+    for r in reqs:
+        assert not callable(r.rho)          # every request was admitted
+        solo = wblbe.Batch(max_cases=1, arena_bytes=1 << 25, max_case_nodes=160 * 160,
+                           tile_x=64, rows_per_tile=16, steps_per_launch=8)
+        cid = solo.admit(r.params, r.rho, r.umax_tol, r.max_steps)
+        while solo.info(cid)["state"] == wblbe.CASE_RUNNING:
+            solo.advance(1)
+        f = solo.get_populations(cid, (r.params.ny, r.params.nx))
+        info = solo.info(cid)
+        solo.close()
+        f_mix, steps, state = got[r.rid]
+        assert steps == info["steps"] and state == info["state"], r.rid
+        assert np.array_equal(f_mix, f), r.rid
