@@ -362,6 +362,10 @@ bool batch_params_valid(const wblbe_batch* b, const wblbe_params* p, char* why, 
              (long long)p->nx * p->ny, b->max_case_nodes);
     return false;
   }
+  if ((long long)case_pitch(p->nx, b->elem) * p->ny >= (1LL << 31)) {
+    snprintf(why, n, "case too large: plane offsets are 32-bit");
+    return false;
+  }
   return true;
 }
 

@@ -29,8 +29,6 @@
 
 namespace wblbe {
 
-constexpr int kRing = 8;          // rows kept in the density ring
-constexpr int kMuRing = 4;        // rows kept in the chemical-potential ring
 constexpr int kHalo = 2;          // density halo radius (mu needs 1, grad mu 2)
 constexpr int kMaxTile = 256;
 
@@ -274,17 +272,32 @@ __host__ __device__ constexpr int dir_cy(int i) {
   return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
 
+// The three directions of each c_iy class: class 0 (c_iy = 0) {0, 1, 3},
+// class 1 (c_iy = +1, pulled from row y-1) {2, 5, 6}, class 2 (c_iy = -1,
+// pulled from row y+1) {4, 7, 8}.  All plane rows of one class come from the
+// same lattice row, so a copy's row offset depends on its class only.
+__host__ __device__ constexpr int class_plane(int cls, int a) {
+  return cls == 0 ? (a == 2 ? 3 : a) : (cls == 1 ? (a == 0 ? 2 : a + 4) : (a == 0 ? 4 : a + 6));
+}
+
+// Rows kept in the density ring and in the chemical-potential ring.  The
+// collision takes rho and grad rho from registers (they are computed with mu
+// from the same 3x3 neighbourhood), so the density ring only holds the rows
+// the mu pass reads; every ring refill is separated from the last read of
+// its slot by a barrier.
+constexpr int kRing = 4;
+constexpr int kMuRing = 4;
+
 // Staging: each loop iteration advances kRows lattice rows per thread; the
 // stage keeps the rows being collided (two behind the density front), the
 // kRows rows being reduced to densities, and kAhead groups of kRows rows in
-// flight.  min_blocks(tx): resident CTAs the register budget must allow, so
-// that shared memory, not registers, sets the occupancy.
+// flight.  min_blocks(tx): resident CTAs the register budget must allow.
 template <typename T> struct Staging;
 template <> struct Staging<float> {
   static constexpr int kRows = 2;
   static constexpr int kAhead = 2;
   static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 8
-  __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 128); }
+  __host__ __device__ static constexpr int min_blocks(int tx) { return 640 / tx > 1 ? 640 / tx : 1; }
 };
 template <> struct Staging<double> {
   static constexpr int kRows = 1;
@@ -300,6 +313,9 @@ __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size
   return 128 + ((size_t)stages * 9 + kRing + kMuRing) * (size_t)(tile + 2 * kPad) * elem;
 }
 
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
+
 // The fused step kernel (MOMENTS = false) and the macroscopic-field /
 // statistics kernel (MOMENTS = true) share one body so that both evaluate
 // rho, mu, F and u with identical arithmetic.
@@ -311,13 +327,15 @@ __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size
 //
 // Pipeline over the rows k = y0-2 .. y1+1 of a strip (y0..y1-1 are the rows
 // this CTA updates), kRows rows per iteration: reduce rows k.. to densities
-// (rho ring), request the rows kRows * kAhead further on, compute mu of rows
-// k-1.. (mu ring), collide and store rows k-2..  Two rows per iteration in
-// FP32 halve the per-row barrier and loop overhead and share the stencil
-// loads of neighbouring rows.
+// (rho ring), request the rows kRows * kAhead further on, compute mu and
+// grad rho of rows k-1.. (mu ring; grad rho stays in registers), collide and
+// store rows k-2..  Two rows per iteration in FP32 halve the per-row barrier
+// and loop overhead and share the stencil loads of neighbouring rows.
 //
-// The strip width TX is a template parameter so that every shared-memory
-// offset is a compile-time constant.
+// Every ring and stage slot repeats after lcm(stages, rings) rows; the row
+// loop is unrolled over that period so that all shared-memory offsets are
+// compile-time constants, and the strip width TX is a template parameter for
+// the same reason.
 // blockDim.x = TX; grid = (ceil(nx / TX), ceil(ny / rows)).
 // Dynamic shared memory: strip_smem_bytes(TX, kStages, sizeof(T)).
 // What one strip pass does with each collided row.
@@ -335,6 +353,7 @@ enum StripMode {
 // chunks through L2 (cp.async.cg), whatever its width: needed when one
 // kernel launch reads data that other CTAs wrote during the same launch (L1
 // is not coherent across SMs).  Requires nx >= 8 and pitch >= nx + 12.
+// Offsets within a plane are 32-bit: pitch * ny < 2^31 (checked by the host).
 template <typename T, bool WB, int MODE, int TX, bool GHOST = false>
 __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restrict__ dst,
                                            const KParams& p, const MomentsOut& mo, int x0,
@@ -344,16 +363,18 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   constexpr bool STATS = MODE != kModeStep;
   constexpr int R = Staging<T>::kRows;     // rows per iteration
   constexpr int PDG = Staging<T>::kAhead;  // row groups requested ahead of use
-  constexpr int kStages = Staging<T>::kStages;
+  constexpr int NST = Staging<T>::kStages;
+  constexpr int NPH = lcm_c(lcm_c(NST, kRing), kMuRing) / R;   // iterations per slot period
+  static_assert(lcm_c(lcm_c(NST, kRing), kMuRing) % R == 0, "slot period");
   constexpr int SW = TX + 2 * kPad;        // row width of every buffer
   constexpr int E = 16 / sizeof(T);        // elements per 16-byte chunk
-  constexpr int NCH = SW / E;              // chunks per plane row
-  constexpr int kMaxChunks = (9 * NCH + TX - 1) / TX;
+  constexpr int NCH = SW / E;              // chunks per plane row (full strip)
+  constexpr int CPT = (3 * NCH + TX - 1) / TX;   // chunks per thread and class
   // 128-byte aligned base (16-byte copies need 16)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
-  T* stage = reinterpret_cast<T*>(base);               // [kStages][9][SW]
-  T* rho_s = stage + kStages * 9 * SW;                 // [kRing][SW]
+  T* stage = reinterpret_cast<T*>(base);               // [NST][9][SW]
+  T* rho_s = stage + NST * 9 * SW;                     // [kRing][SW]
   T* mu_s = rho_s + kRing * SW;                        // [kMuRing][SW]
 
   const int tx = threadIdx.x;
@@ -370,34 +391,36 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   const bool use_vec = GHOST || ((w == TX) && (p.nx % 4 == 0));
   // 16-byte chunks per plane row this strip needs (its columns plus 4 on
   // each side, rounded up to whole chunks; never past the stage row)
-  const int nch_rt = GHOST ? (w + 2 * kPad + (16 / (int)sizeof(T)) - 1) / (16 / (int)sizeof(T))
-                           : (TX + 2 * kPad) / (16 / (int)sizeof(T));
+  const int nch_rt = GHOST ? (w + 2 * kPad + E - 1) / E : NCH;
 
   const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa6 = T(p.kappa / 6.0);
   const CollideConsts<T> cc(p);
   const int kfirst = y0 - 2, klast = y1 + 1;
 
-  // 16-byte chunks this thread copies in every row (fixed per thread): chunk
-  // j of plane i covers columns x0-4+jE .. x0-4+jE+E-1, which wrap only as a
-  // whole (nx % 4 == 0).
-  const T* ch_src[kMaxChunks];
-  int ch_dst[kMaxChunks], ch_dy[kMaxChunks];
-  bool ch_on[kMaxChunks];
+  // 16-byte chunks this thread copies in every row (fixed per thread): in
+  // class c, chunk q = tx + m * TX is chunk j of the class's plane a, covering
+  // columns x0-4+jE .. x0-4+jE+E-1, which wrap only as a whole (nx % 4 == 0).
+  const T* ch_src[3][CPT];
+  int ch_dst[3][CPT];
+  bool ch_on[3][CPT];
 #pragma unroll
-  for (int c = 0; c < kMaxChunks; ++c) {
-    const int q = tx + c * TX;
-    ch_on[c] = use_vec && q < 9 * nch_rt;
-    const int i = ch_on[c] ? q / nch_rt : 0, j = ch_on[c] ? q - i * nch_rt : 0;
-    int col = x0 - kPad + j * E;
-    if (GHOST) {
-      col += kPad;                         // storage offset of column x is x + 4
-    } else {
-      if (col < 0) col += p.nx;
-      else if (col >= p.nx) col -= p.nx;
+  for (int cls = 0; cls < 3; ++cls) {
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+      const int q = tx + m * TX;
+      ch_on[cls][m] = use_vec && q < 3 * nch_rt;
+      const int a = ch_on[cls][m] ? q / nch_rt : 0, j = ch_on[cls][m] ? q - a * nch_rt : 0;
+      const int i = class_plane(cls, a);
+      int col = x0 - kPad + j * E;
+      if (GHOST) {
+        col += kPad;                       // storage offset of column x is x + 4
+      } else {
+        if (col < 0) col += p.nx;
+        else if (col >= p.nx) col -= p.nx;
+      }
+      ch_src[cls][m] = src + i * p.plane + col;
+      ch_dst[cls][m] = i * SW + j * E;
     }
-    ch_src[c] = src + i * p.plane + col;
-    ch_dst[c] = i * SW + j * E;
-    ch_dy[c] = dir_cy(i);
   }
 
   // Request the next logical row (its plane rows r - c_iy) into stage slot
@@ -411,10 +434,11 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
     T* st = stage + slot * 9 * SW;
     if (use_vec) {
 #pragma unroll
-      for (int c = 0; c < kMaxChunks; ++c) {
-        if (!ch_on[c]) continue;
-        const int roff = ch_dy[c] == 0 ? row_0 : (ch_dy[c] > 0 ? row_m : row_p);
-        cp_async16(st + ch_dst[c], ch_src[c] + roff);
+      for (int cls = 0; cls < 3; ++cls) {
+        const int roff = cls == 0 ? row_0 : (cls == 1 ? row_m : row_p);
+#pragma unroll
+        for (int m = 0; m < CPT; ++m)
+          if (ch_on[cls][m]) cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
       }
     } else {
       const int ncols = w + 2 * kPad;
@@ -438,141 +462,148 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
            ((st[4 * SW + s] + st[5 * SW + s - 1]) + (st[6 * SW + s + 1] + st[7 * SW + s + 1])) +
            st[8 * SW + s - 1];
   };
-  // mu of logical row r at slots 3 .. w+4 (own slot; threads mu_lo and
-  // mu_hi also take slots 3 and w+4).
-  auto put_mu = [&](int r) {
-    const T* rn = rho_s + ((r + 1) & (kRing - 1)) * SW;  // row above (y+1)
-    const T* rc = rho_s + (r & (kRing - 1)) * SW;
-    const T* rsb = rho_s + ((r - 1) & (kRing - 1)) * SW; // row below (y-1)
-    T* mrow = mu_s + (r & (kMuRing - 1)) * SW;
-    auto at = [&](int s) {
-      return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
-                         rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
-    };
-    if (own) mrow[sx] = at(sx);
-    if (tx == mu_lo) mrow[3] = at(3);
-    if (tx == mu_hi) mrow[w + 4] = at(w + 4);
-  };
 
   double st_mass = 0.0, st_kin = 0.0, st_u2 = 0.0;
   double st_mumin = 1e300, st_mumax = -1e300;
   int st_bad = 0;
 
-  // Rows kfirst .. klast2 are processed in groups of R (klast2 >= klast; a
-  // row past klast only feeds values nobody reads).
+  // Rows kfirst .. kfirst + nlast are processed in groups of R (a row past
+  // klast only feeds values nobody reads).
   const int ngroups = (klast - kfirst + R) / R;
-  const int klast2 = kfirst + R * ngroups - 1;
-  auto wrap_slot = [](int sl) { return sl >= kStages ? sl - kStages : sl; };
+  const int nlast = R * ngroups - 1;       // last row, relative to kfirst
 
-  // running output positions of the next row to collide
-  T* out_row = dst + (long long)y0 * p.pitch + x0 + tx + (GHOST ? kPad : 0);
-  // ghost copies a boundary column also writes (storage offsets relative to
-  // its own): x < 4 -> +nx (right ghost), x >= nx - 4 -> -nx (left ghost)
+  // store position of column x0 + tx within a plane; ghost copies a boundary
+  // column also writes: x < 4 -> +nx (right ghost), x >= nx - 4 -> -nx (left)
+  const int xcol = x0 + tx + (GHOST ? kPad : 0);
   const int xg = x0 + tx;
   const bool ghost_r = GHOST && own && xg < kPad;
   const bool ghost_l = GHOST && own && xg >= p.nx - kPad;
-  long long mom_row = (long long)y0 * p.nx + x0 + tx;
 
-  int sq = 0;                              // stage slot of the next requested row
-  for (int gq = 0; gq < PDG; ++gq) {
+  {
+    int sq = 0;                            // stage slot of the next requested row
+    for (int gq = 0; gq < PDG; ++gq) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (kfirst + gq * R + j <= klast2) request_next(sq);
-      sq = wrap_slot(sq + 1);
+      for (int j = 0; j < R; ++j) {
+        if (gq * R + j <= nlast) request_next(sq);
+        ++sq;
+      }
+      cp_async_commit();                   // one group per R rows, possibly empty
     }
-    cp_async_commit();                     // one group per R rows, possibly empty
   }
   cp_async_wait<PDG - 1>();                // first group landed (this thread)
   __syncthreads();                         // ... and everyone else's
 
-  int sk = 0;                              // stage slot of row k
-  int sc = kStages - 2;                    // stage slot of row k - 2
-  for (int k = kfirst; k <= klast2; k += R) {
+  // rho and grad rho of the last mu row of the previous iteration
+  T prs = T(0), pgx = T(0), pgy = T(0);
+  bool live = true;
+  for (int n = 0; live; n += NPH * R) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const T* st = stage + wrap_slot(sk + j) * 9 * SW;
-      T* row = rho_s + ((k + j) & (kRing - 1)) * SW;
-      if (own) row[sx] = staged_rho(st, sx);
-      if (halo) row[hs] = staged_rho(st, hs);
-    }
-    // barrier B: every read of the stage slots about to be refilled (rows
-    // collided an iteration ago) is done
-    __syncthreads();
+    for (int ph = 0; ph < NPH; ++ph) {
+      const int n0 = n + ph * R;           // density front, relative to kfirst
+      if (live && n0 > nlast) live = false;
+      if (live) {
+        // slot of the row at relative offset d from this iteration's front
+        // (ph * R + d, taken modulo the ring; compile-time after unrolling)
+#define WB_SLOT(d, ring) ((ph * R + (d) + 4 * (ring)) % (ring))
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (k + R * PDG + j <= klast2) request_next(sq);
-      sq = wrap_slot(sq + 1);
-    }
-    cp_async_commit();
-    cp_async_wait<PDG - 1>();              // next group landed (visible after barrier C)
+        for (int j = 0; j < R; ++j) {
+          const T* st = stage + WB_SLOT(j, NST) * 9 * SW;
+          T* row = rho_s + WB_SLOT(j, kRing) * SW;
+          if (own) row[sx] = staged_rho(st, sx);
+          if (halo) row[hs] = staged_rho(st, hs);
+        }
+        // barrier B: every read of the stage slots about to be refilled (rows
+        // collided an iteration ago) and of the mu ring rows about to be
+        // rewritten is done
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < R; ++j)
-      if (k - 1 + j >= y0 - 1) put_mu(k - 1 + j);
-    __syncthreads();
+        for (int j = 0; j < R; ++j)
+          if (n0 + R * PDG + j <= nlast) request_next(WB_SLOT(R * PDG + j, NST));
+        cp_async_commit();
+        cp_async_wait<PDG - 1>();          // next group landed (visible after barrier C)
+        // mu (ring) and rho, grad rho (registers) of rows n0-1+j
+        T frs[R], fgx[R], fgy[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const int c = k - 2 + j;             // row to collide
-      if (c >= y0 && c < y1 && own) {
-        const T* r_dn = rho_s + ((c - 1) & (kRing - 1)) * SW;
-        const T* r_c = rho_s + (c & (kRing - 1)) * SW;
-        const T* r_up = rho_s + ((c + 1) & (kRing - 1)) * SW;
-        const T* m_dn = mu_s + ((c - 1) & (kMuRing - 1)) * SW;
-        const T* m_c = mu_s + (c & (kMuRing - 1)) * SW;
-        const T* m_up = mu_s + ((c + 1) & (kMuRing - 1)) * SW;
-        // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
-        T gmx, gmy, grx, gry;
-        iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1], m_up[sx - 1],
-                    m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
-        iso_grad<T>(r_c[sx + 1], r_c[sx - 1], r_up[sx], r_dn[sx], r_up[sx + 1], r_up[sx - 1],
-                    r_dn[sx + 1], r_dn[sx - 1], grx, gry);
-        const T rs = r_c[sx];
-        const T* st = stage + wrap_slot(sc + j) * 9 * SW;
-        // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
-        T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
-                  st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
-                  st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
-        T ux, uy;
-        collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
-        if (!MOMENTS) {
-          T* out = out_row + (long long)j * p.pitch;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            *out = g[i];
-            if (ghost_r) out[p.nx] = g[i];
-            if (ghost_l) out[-p.nx] = g[i];
-            out += p.plane;
+        for (int j = 0; j < R; ++j) {
+          frs[j] = fgx[j] = fgy[j] = T(0);
+          if (kfirst + n0 - 1 + j >= y0 - 1) {
+            const T* rn = rho_s + WB_SLOT(j, kRing) * SW;       // row above (y+1)
+            const T* rc = rho_s + WB_SLOT(j - 1, kRing) * SW;
+            const T* rsb = rho_s + WB_SLOT(j - 2, kRing) * SW;  // row below (y-1)
+            T* mrow = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
+            auto at = [&](int s) {
+              return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
+                                 rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
+            };
+            if (own) {
+              mrow[sx] = at(sx);
+              frs[j] = rc[sx];
+              iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
+                          rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+            }
+            if (tx == mu_lo) mrow[3] = at(3);
+            if (tx == mu_hi) mrow[w + 4] = at(w + 4);
           }
         }
-        if (STATS) {
-          const double rho = (double)rs + p.rho_ref;
-          const double mu = (double)m_c[sx];
-          const double dux = (double)ux, duy = (double)uy;
-          if (MOMENTS) {
-            const long long kk = mom_row + (long long)j * p.nx;
-            if (mo.rho) mo.rho[kk] = rho;
-            if (mo.ux) mo.ux[kk] = dux;
-            if (mo.uy) mo.uy[kk] = duy;
-            if (mo.mu) mo.mu[kk] = mu;
+        __syncthreads();                   // barrier C
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          const int c = kfirst + n0 - 2 + j;   // row to collide
+          if (c >= y0 && c < y1 && own) {
+            const T* m_dn = mu_s + WB_SLOT(j - 3, kMuRing) * SW;
+            const T* m_c = mu_s + WB_SLOT(j - 2, kMuRing) * SW;
+            const T* m_up = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
+            // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
+            T gmx, gmy;
+            iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1],
+                        m_up[sx - 1], m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
+            const T rs = j == 0 ? prs : frs[j - 1];
+            const T grx = j == 0 ? pgx : fgx[j - 1];
+            const T gry = j == 0 ? pgy : fgy[j - 1];
+            const T* st = stage + WB_SLOT(j - 2, NST) * 9 * SW;
+            // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
+            T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
+                      st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
+                      st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
+            T ux, uy;
+            collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+            if (!MOMENTS) {
+              const unsigned off = (unsigned)(c * p.pitch + xcol);
+#pragma unroll
+              for (int i = 0; i < 9; ++i) {
+                T* di = dst + i * p.plane;
+                di[off] = g[i];
+                if (ghost_r) di[off + p.nx] = g[i];
+                if (ghost_l) di[off - p.nx] = g[i];
+              }
+            }
+            if (STATS) {
+              const double rho = (double)rs + p.rho_ref;
+              const double mu = (double)m_c[sx];
+              const double dux = (double)ux, duy = (double)uy;
+              if (MOMENTS) {
+                const unsigned kk = (unsigned)(c * p.nx + x0 + tx);
+                if (mo.rho) mo.rho[kk] = rho;
+                if (mo.ux) mo.ux[kk] = dux;
+                if (mo.uy) mo.uy[kk] = duy;
+                if (mo.mu) mo.mu[kk] = mu;
+              }
+              const double u2 = dux * dux + duy * duy;
+              st_mass += rho;
+              st_kin += 0.5 * rho * u2;
+              st_u2 = fmax(st_u2, u2);
+              st_mumin = fmin(st_mumin, mu);
+              st_mumax = fmax(st_mumax, mu);
+              if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
+            }
           }
-          const double u2 = dux * dux + duy * duy;
-          st_mass += rho;
-          st_kin += 0.5 * rho * u2;
-          st_u2 = fmax(st_u2, u2);
-          st_mumin = fmin(st_mumin, mu);
-          st_mumax = fmax(st_mumax, mu);
-          if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
         }
+        prs = frs[R - 1];
+        pgx = fgx[R - 1];
+        pgy = fgy[R - 1];
+#undef WB_SLOT
       }
     }
-    // advance the output positions by the rows collided in this iteration
-    {
-      const int c0 = k - 2;
-      const int ndone = max(0, min(c0 + R, y1) - max(c0, y0));
-      out_row += (long long)ndone * p.pitch;
-      mom_row += (long long)ndone * p.nx;
-    }
-    sk = wrap_slot(sk + R);
-    sc = wrap_slot(sc + R);
   }
   cp_async_wait<0>();
 
