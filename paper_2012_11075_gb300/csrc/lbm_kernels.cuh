@@ -236,6 +236,122 @@ __device__ __forceinline__ void iso_grad(T e, T w, T n, T s, T ne, T nw, T se, T
   gy = T(1.0 / 3.0) * (n - s) + T(1.0 / 12.0) * (d1 - d2);
 }
 
+// ---- packed FP32 pairs ------------------------------------------------------
+//
+// In FP32 a thread advances two lattice rows per iteration; their arithmetic
+// is identical, so it runs on float2 pairs (x: the lower row, y: the upper
+// row) with the paired FP32 instructions of sm_100 and later, one instruction
+// for both rows.  Each lane is an ordinary IEEE single-precision operation,
+// so a row's result does not depend on which lane it occupies.
+__device__ __forceinline__ float2 splat(float c) { return make_float2(c, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// chem_pot on a pair of nodes (same formula and evaluation order)
+__device__ __forceinline__ float2 chem_pot_x2(float2 c, float2 e, float2 w, float2 n, float2 s,
+                                              float2 ne, float2 nw, float2 se, float2 sw,
+                                              float2 two_beta, float2 dl, float2 dg,
+                                              float2 kappa6) {
+  const float2 a = add2(c, dl), b = add2(c, dg);
+  const float2 mu0 = mul2(mul2(mul2(two_beta, a), b), add2(a, b));
+  const float2 lap6 = fma2(splat(-20.0f), c,
+                           fma2(splat(4.0f), add2(add2(e, w), add2(n, s)),
+                                add2(add2(ne, nw), add2(se, sw))));
+  return fma2(kappa6, make_float2(-lap6.x, -lap6.y), mu0);
+}
+
+// iso_grad on a pair of nodes
+__device__ __forceinline__ void iso_grad_x2(float2 e, float2 w, float2 n, float2 s, float2 ne,
+                                            float2 nw, float2 se, float2 sw, float2& gx,
+                                            float2& gy) {
+  const float2 d1 = sub2(ne, sw), d2 = sub2(se, nw);
+  gx = fma2(splat(1.0f / 3.0f), sub2(e, w), mul2(splat(1.0f / 12.0f), add2(d1, d2)));
+  gy = fma2(splat(1.0f / 3.0f), sub2(n, s), mul2(splat(1.0f / 12.0f), sub2(d1, d2)));
+}
+
+// collide<float, WB> on a pair of nodes (FP32-shifted storage): the same
+// terms as the scalar version, with the multiply-adds written out.
+template <bool WB>
+__device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx, float2 gmy,
+                                           float2 grx, float2 gry, const CollideConsts<float>& q,
+                                           float2& ux_out, float2& uy_out) {
+  const float2 omega = splat(q.omega), kf = splat(q.kf), third = splat(1.0f / 3.0f);
+  const float2 rho = add2(rs, splat(q.rho_ref));
+  const float2 nrho = sub2(splat(-q.rho_ref), rs);        // -rho
+  float2 Fx, Fy;
+  if (WB) {
+    Fx = mul2(nrho, gmx);                                 // Eq. mF
+    Fy = mul2(nrho, gmy);
+  } else {
+    Fx = fma2(third, grx, mul2(nrho, gmx));               // potential form
+    Fy = fma2(third, gry, mul2(nrho, gmy));
+  }
+  const float2 d13 = sub2(g[1], g[3]), d24 = sub2(g[2], g[4]);
+  const float2 d57 = sub2(g[5], g[7]), d86 = sub2(g[8], g[6]);
+  const float2 jx = add2(add2(d13, d57), d86);
+  const float2 jy = sub2(add2(d24, d57), d86);
+  const float2 inv_rho = make_float2(recip(rho.x), recip(rho.y));
+  const float2 half = splat(0.5f);
+  const float2 ux = mul2(fma2(half, Fx, jx), inv_rho);   // Eq. rhoU
+  const float2 uy = mul2(fma2(half, Fy, jy), inv_rho);
+  ux_out = ux;
+  uy_out = uy;
+
+  float2 Gx = Fx, Gy = Fy;
+  if (WB) {
+    Gx = fma2(third, grx, Fx);
+    Gy = fma2(third, gry, Fy);
+  }
+  const float2 orho = mul2(omega, rho);
+  const float2 uu = fma2(ux, ux, mul2(uy, uy));
+  const float2 uG = fma2(ux, Gx, mul2(uy, Gy));
+  const float2 t = fma2(mul2(splat(-1.5f), orho), uu, mul2(splat(q.kf_m3), uG));
+
+  float2 Cax, Cdg;
+  if (WB) {
+    const float2 ku = mul2(kf, fma2(ux, grx, mul2(uy, gry)));
+    Cax = mul2(splat(1.0f / 9.0f), fma2(half, ku, t));
+    Cdg = mul2(splat(1.0f / 36.0f), fma2(splat(2.0f), ku, t));
+  } else {
+    const float2 s = fma2(omega, rs, t);                 // b_i = w_i rs
+    Cax = mul2(splat(1.0f / 9.0f), s);
+    Cdg = mul2(splat(1.0f / 36.0f), s);
+  }
+  const float2 hrho = mul2(half, orho);
+  const float2 kGx = mul2(kf, Gx), kGy = mul2(kf, Gy);
+  const float2 Mx = fma2(orho, ux, mul2(kf, Fx));
+  const float2 My = fma2(orho, uy, mul2(kf, Fy));
+
+  const float2 E1 = fma2(ux, fma2(hrho, ux, kGx), Cax);
+  const float2 O1 = mul2(third, Mx);
+  const float2 E2 = fma2(uy, fma2(hrho, uy, kGy), Cax);
+  const float2 O2 = mul2(third, My);
+  const float2 quarter = splat(0.25f), twelfth = splat(1.0f / 12.0f);
+  const float2 cu5 = add2(ux, uy);
+  const float2 E5 = fma2(mul2(quarter, cu5), fma2(hrho, cu5, add2(kGx, kGy)), Cdg);
+  const float2 O5 = mul2(twelfth, add2(Mx, My));
+  const float2 cu6 = sub2(uy, ux);
+  const float2 E6 = fma2(mul2(quarter, cu6), fma2(hrho, cu6, sub2(kGy, kGx)), Cdg);
+  const float2 O6 = mul2(twelfth, sub2(My, Mx));
+
+  const float2 keep = splat(q.keep);
+  g[1] = fma2(keep, g[1], add2(E1, O1));
+  g[3] = fma2(keep, g[3], sub2(E1, O1));
+  g[2] = fma2(keep, g[2], add2(E2, O2));
+  g[4] = fma2(keep, g[4], sub2(E2, O2));
+  g[5] = fma2(keep, g[5], add2(E5, O5));
+  g[7] = fma2(keep, g[7], sub2(E5, O5));
+  g[6] = fma2(keep, g[6], add2(E6, O6));
+  g[8] = fma2(keep, g[8], sub2(E6, O6));
+  // rest population from the node mass balance, as in the scalar version
+  g[0] = sub2(rs, add2(add2(add2(g[1], g[3]), add2(g[2], g[4])),
+                       add2(add2(g[5], g[7]), add2(g[6], g[8]))));
+}
+
 // ---- asynchronous copies into shared memory -------------------------------
 //
 // The pulled plane rows are copied global -> shared with cp.async (no
@@ -493,8 +609,49 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   cp_async_wait<PDG - 1>();                // first group landed (this thread)
   __syncthreads();                         // ... and everyone else's
 
-  // rho and grad rho of the last mu row of the previous iteration
+  // One collided node: store (or write the moment fields) and fold the stats.
+  auto emit = [&](int c, const T (&gv)[9], T rs, T muc, T ux, T uy) {
+    if (!MOMENTS) {
+      const unsigned off = (unsigned)(c * p.pitch + xcol);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        T* di = dst + i * p.plane;
+        di[off] = gv[i];
+        if (ghost_r) di[off + p.nx] = gv[i];
+        if (ghost_l) di[off - p.nx] = gv[i];
+      }
+    }
+    if (STATS) {
+      const double rho = (double)rs + p.rho_ref;
+      const double mu = (double)muc;
+      const double dux = (double)ux, duy = (double)uy;
+      if (MOMENTS) {
+        const unsigned kk = (unsigned)(c * p.nx + x0 + tx);
+        if (mo.rho) mo.rho[kk] = rho;
+        if (mo.ux) mo.ux[kk] = dux;
+        if (mo.uy) mo.uy[kk] = duy;
+        if (mo.mu) mo.mu[kk] = mu;
+      }
+      const double u2 = dux * dux + duy * duy;
+      st_mass += rho;
+      st_kin += 0.5 * rho * u2;
+      st_u2 = fmax(st_u2, u2);
+      st_mumin = fmin(st_mumin, mu);
+      st_mumax = fmax(st_mumax, mu);
+      if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
+    }
+  };
+
+  // FP32: the two rows of an iteration run as float2 pairs
+  constexpr bool kPacked = sizeof(T) == 4 && R == 2;
+  // rho and grad rho of the last mu row(s) of the previous iteration
   T prs = T(0), pgx = T(0), pgy = T(0);
+  float2 prs2 = make_float2(0.f, 0.f), pgx2 = prs2, pgy2 = prs2;
+  const float2 tb2 = make_float2((float)two_beta, (float)two_beta);
+  const float2 dl2 = make_float2((float)dl, (float)dl), dg2 = make_float2((float)dg, (float)dg);
+  const float2 k62 = make_float2((float)kappa6, (float)kappa6);
+  // pair (lo[s], hi[s]) of two buffer rows
+  auto V = [](const T* lo, const T* hi, int s) { return make_float2((float)lo[s], (float)hi[s]); };
   bool live = true;
   for (int n = 0; live; n += NPH * R) {
 #pragma unroll
@@ -505,12 +662,37 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
         // slot of the row at relative offset d from this iteration's front
         // (ph * R + d, taken modulo the ring; compile-time after unrolling)
 #define WB_SLOT(d, ring) ((ph * R + (d) + 4 * (ring)) % (ring))
+        if constexpr (kPacked) {
+          const T* s0 = stage + WB_SLOT(0, NST) * 9 * SW;
+          const T* s1 = stage + WB_SLOT(1, NST) * 9 * SW;
+          T* r0 = rho_s + WB_SLOT(0, kRing) * SW;
+          T* r1 = rho_s + WB_SLOT(1, kRing) * SW;
+          // same summation order as staged_rho
+          auto rho2 = [&](int s) {
+            const float2 a = add2(add2(V(s0, s1, 0 * SW + s), V(s0, s1, 1 * SW + s - 1)),
+                                  add2(V(s0, s1, 2 * SW + s), V(s0, s1, 3 * SW + s + 1)));
+            const float2 b = add2(add2(V(s0, s1, 4 * SW + s), V(s0, s1, 5 * SW + s - 1)),
+                                  add2(V(s0, s1, 6 * SW + s + 1), V(s0, s1, 7 * SW + s + 1)));
+            return add2(add2(a, b), V(s0, s1, 8 * SW + s - 1));
+          };
+          if (own) {
+            const float2 v = rho2(sx);
+            r0[sx] = v.x;
+            r1[sx] = v.y;
+          }
+          if (halo) {
+            const float2 v = rho2(hs);
+            r0[hs] = v.x;
+            r1[hs] = v.y;
+          }
+        } else {
 #pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const T* st = stage + WB_SLOT(j, NST) * 9 * SW;
-          T* row = rho_s + WB_SLOT(j, kRing) * SW;
-          if (own) row[sx] = staged_rho(st, sx);
-          if (halo) row[hs] = staged_rho(st, hs);
+          for (int j = 0; j < R; ++j) {
+            const T* st = stage + WB_SLOT(j, NST) * 9 * SW;
+            T* row = rho_s + WB_SLOT(j, kRing) * SW;
+            if (own) row[sx] = staged_rho(st, sx);
+            if (halo) row[hs] = staged_rho(st, hs);
+          }
         }
         // barrier B: every read of the stage slots about to be refilled (rows
         // collided an iteration ago) and of the mu ring rows about to be
@@ -521,86 +703,134 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
           if (n0 + R * PDG + j <= nlast) request_next(WB_SLOT(R * PDG + j, NST));
         cp_async_commit();
         cp_async_wait<PDG - 1>();          // next group landed (visible after barrier C)
+
         // mu (ring) and rho, grad rho (registers) of rows n0-1+j
         T frs[R], fgx[R], fgy[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          frs[j] = fgx[j] = fgy[j] = T(0);
-          if (kfirst + n0 - 1 + j >= y0 - 1) {
-            const T* rn = rho_s + WB_SLOT(j, kRing) * SW;       // row above (y+1)
-            const T* rc = rho_s + WB_SLOT(j - 1, kRing) * SW;
-            const T* rsb = rho_s + WB_SLOT(j - 2, kRing) * SW;  // row below (y-1)
-            T* mrow = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
-            auto at = [&](int s) {
-              return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
-                                 rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
+        float2 frs2 = make_float2(0.f, 0.f), fgx2 = frs2, fgy2 = frs2;
+        if constexpr (kPacked) {
+          // lane x: row n0-1, lane y: row n0 (rows below n0-1 feed nothing)
+          if (kfirst + n0 >= y0 - 1) {
+            const T* rb = rho_s + WB_SLOT(-2, kRing) * SW;   // row n0-2
+            const T* rc = rho_s + WB_SLOT(-1, kRing) * SW;   // row n0-1
+            const T* ra = rho_s + WB_SLOT(0, kRing) * SW;    // row n0
+            const T* rt = rho_s + WB_SLOT(1, kRing) * SW;    // row n0+1
+            T* m0 = mu_s + WB_SLOT(-1, kMuRing) * SW;
+            T* m1 = mu_s + WB_SLOT(0, kMuRing) * SW;
+            auto at2 = [&](int s) {
+              return chem_pot_x2(V(rc, ra, s), V(rc, ra, s + 1), V(rc, ra, s - 1), V(ra, rt, s),
+                                 V(rb, rc, s), V(ra, rt, s + 1), V(ra, rt, s - 1),
+                                 V(rb, rc, s + 1), V(rb, rc, s - 1), tb2, dl2, dg2, k62);
             };
             if (own) {
-              mrow[sx] = at(sx);
-              frs[j] = rc[sx];
-              iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
-                          rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+              const float2 mu = at2(sx);
+              m0[sx] = mu.x;
+              m1[sx] = mu.y;
+              frs2 = V(rc, ra, sx);
+              iso_grad_x2(V(rc, ra, sx + 1), V(rc, ra, sx - 1), V(ra, rt, sx), V(rb, rc, sx),
+                          V(ra, rt, sx + 1), V(ra, rt, sx - 1), V(rb, rc, sx + 1),
+                          V(rb, rc, sx - 1), fgx2, fgy2);
             }
-            if (tx == mu_lo) mrow[3] = at(3);
-            if (tx == mu_hi) mrow[w + 4] = at(w + 4);
+            if (tx < 2) {                  // halo mu at slots 3 and w+4
+              const int s = tx == 0 ? 3 : w + 4;
+              const float2 mu = at2(s);
+              m0[s] = mu.x;
+              m1[s] = mu.y;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            frs[j] = fgx[j] = fgy[j] = T(0);
+            if (kfirst + n0 - 1 + j >= y0 - 1) {
+              const T* rn = rho_s + WB_SLOT(j, kRing) * SW;       // row above (y+1)
+              const T* rc = rho_s + WB_SLOT(j - 1, kRing) * SW;
+              const T* rsb = rho_s + WB_SLOT(j - 2, kRing) * SW;  // row below (y-1)
+              T* mrow = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
+              auto at = [&](int s) {
+                return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
+                                   rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
+              };
+              if (own) {
+                mrow[sx] = at(sx);
+                frs[j] = rc[sx];
+                iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
+                            rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+              }
+              if (tx == mu_lo) mrow[3] = at(3);
+              if (tx == mu_hi) mrow[w + 4] = at(w + 4);
+            }
           }
         }
         __syncthreads();                   // barrier C
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int c = kfirst + n0 - 2 + j;   // row to collide
-          if (c >= y0 && c < y1 && own) {
-            const T* m_dn = mu_s + WB_SLOT(j - 3, kMuRing) * SW;
-            const T* m_c = mu_s + WB_SLOT(j - 2, kMuRing) * SW;
-            const T* m_up = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
-            // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
-            T gmx, gmy;
-            iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1],
-                        m_up[sx - 1], m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
-            const T rs = j == 0 ? prs : frs[j - 1];
-            const T grx = j == 0 ? pgx : fgx[j - 1];
-            const T gry = j == 0 ? pgy : fgy[j - 1];
-            const T* st = stage + WB_SLOT(j - 2, NST) * 9 * SW;
+
+        if constexpr (kPacked) {
+          const int c0 = kfirst + n0 - 2;    // rows c0 (lane x) and c0+1 (lane y)
+          const bool v0 = c0 >= y0 && c0 < y1, v1 = c0 + 1 >= y0 && c0 + 1 < y1;
+          if (own && (v0 || v1)) {
+            const T* mA = mu_s + WB_SLOT(-3, kMuRing) * SW;    // row c0-1
+            const T* mB = mu_s + WB_SLOT(-2, kMuRing) * SW;    // row c0
+            const T* mC = mu_s + WB_SLOT(-1, kMuRing) * SW;    // row c0+1
+            const T* mD = mu_s + WB_SLOT(0, kMuRing) * SW;     // row c0+2
+            float2 gmx, gmy;
+            iso_grad_x2(V(mB, mC, sx + 1), V(mB, mC, sx - 1), V(mC, mD, sx), V(mA, mB, sx),
+                        V(mC, mD, sx + 1), V(mC, mD, sx - 1), V(mA, mB, sx + 1),
+                        V(mA, mB, sx - 1), gmx, gmy);
+            // rho, grad rho of row c0 come from the previous iteration's lane y
+            const float2 rs = make_float2(prs2.y, frs2.x);
+            const float2 grx = make_float2(pgx2.y, fgx2.x), gry = make_float2(pgy2.y, fgy2.x);
+            const T* s0 = stage + WB_SLOT(-2, NST) * 9 * SW;
+            const T* s1 = stage + WB_SLOT(-1, NST) * 9 * SW;
             // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
-            T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
-                      st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
-                      st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
-            T ux, uy;
-            collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
-            if (!MOMENTS) {
-              const unsigned off = (unsigned)(c * p.pitch + xcol);
-#pragma unroll
-              for (int i = 0; i < 9; ++i) {
-                T* di = dst + i * p.plane;
-                di[off] = g[i];
-                if (ghost_r) di[off + p.nx] = g[i];
-                if (ghost_l) di[off - p.nx] = g[i];
-              }
+            float2 g[9] = {V(s0, s1, 0 * SW + sx),     V(s0, s1, 1 * SW + sx - 1),
+                           V(s0, s1, 2 * SW + sx),     V(s0, s1, 3 * SW + sx + 1),
+                           V(s0, s1, 4 * SW + sx),     V(s0, s1, 5 * SW + sx - 1),
+                           V(s0, s1, 6 * SW + sx + 1), V(s0, s1, 7 * SW + sx + 1),
+                           V(s0, s1, 8 * SW + sx - 1)};
+            float2 ux, uy;
+            collide_x2<WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+            if (v0) {
+              const T gl[9] = {g[0].x, g[1].x, g[2].x, g[3].x, g[4].x,
+                               g[5].x, g[6].x, g[7].x, g[8].x};
+              emit(c0, gl, rs.x, STATS ? mB[sx] : T(0), ux.x, uy.x);
             }
-            if (STATS) {
-              const double rho = (double)rs + p.rho_ref;
-              const double mu = (double)m_c[sx];
-              const double dux = (double)ux, duy = (double)uy;
-              if (MOMENTS) {
-                const unsigned kk = (unsigned)(c * p.nx + x0 + tx);
-                if (mo.rho) mo.rho[kk] = rho;
-                if (mo.ux) mo.ux[kk] = dux;
-                if (mo.uy) mo.uy[kk] = duy;
-                if (mo.mu) mo.mu[kk] = mu;
-              }
-              const double u2 = dux * dux + duy * duy;
-              st_mass += rho;
-              st_kin += 0.5 * rho * u2;
-              st_u2 = fmax(st_u2, u2);
-              st_mumin = fmin(st_mumin, mu);
-              st_mumax = fmax(st_mumax, mu);
-              if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
+            if (v1) {
+              const T gh[9] = {g[0].y, g[1].y, g[2].y, g[3].y, g[4].y,
+                               g[5].y, g[6].y, g[7].y, g[8].y};
+              emit(c0 + 1, gh, rs.y, STATS ? mC[sx] : T(0), ux.y, uy.y);
             }
           }
+          prs2 = frs2;
+          pgx2 = fgx2;
+          pgy2 = fgy2;
+        } else {
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int c = kfirst + n0 - 2 + j;   // row to collide
+            if (c >= y0 && c < y1 && own) {
+              const T* m_dn = mu_s + WB_SLOT(j - 3, kMuRing) * SW;
+              const T* m_c = mu_s + WB_SLOT(j - 2, kMuRing) * SW;
+              const T* m_up = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
+              // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
+              T gmx, gmy;
+              iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1],
+                          m_up[sx - 1], m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
+              const T rs = j == 0 ? prs : frs[j - 1];
+              const T grx = j == 0 ? pgx : fgx[j - 1];
+              const T gry = j == 0 ? pgy : fgy[j - 1];
+              const T* st = stage + WB_SLOT(j - 2, NST) * 9 * SW;
+              // f_i(x) = P_i(x - c_i): column offset -c_ix within the staged rows
+              T g[9] = {st[0 * SW + sx],     st[1 * SW + sx - 1], st[2 * SW + sx],
+                        st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
+                        st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
+              T ux, uy;
+              collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+              emit(c, g, rs, STATS ? m_c[sx] : T(0), ux, uy);
+            }
+          }
+          prs = frs[R - 1];
+          pgx = fgx[R - 1];
+          pgy = fgy[R - 1];
         }
-        prs = frs[R - 1];
-        pgx = fgx[R - 1];
-        pgy = fgy[R - 1];
 #undef WB_SLOT
       }
     }
