@@ -498,12 +498,13 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   const bool own = tx < w;
   __syncthreads();                         // a previous pass may still read smem
   const int sx = tx + kPad;                // slot of the own column
-  // Halo work, kept in warp 0 (threads 0-3 take the densities of slots 2, 3
-  // (x0-2, x0-1) and w+4, w+5 (x0+w, x0+w+1); threads 0 and 1 take mu at
-  // slots 3 and w+4): one warp runs the halo branch instead of all of them.
+  // Halo work: threads 0-3 take the densities of slots 2, 3 (x0-2, x0-1)
+  // and w+4, w+5 (x0+w, x0+w+1); threads mu_lo and mu_hi (warp 1 when there
+  // is one) take mu at slots 3 and w+4.  Each halo branch runs in one warp,
+  // and the two are in different warps so that no warp carries both.
   const bool halo = tx < 4;
   const int hs = tx < 2 ? 2 + tx : w + 2 + tx;
-  const int mu_lo = 0, mu_hi = 1;
+  constexpr int mu_lo = TX >= 64 ? 32 : 0, mu_hi = mu_lo + 1;
   const bool use_vec = GHOST || ((w == TX) && (p.nx % 4 == 0));
   // 16-byte chunks per plane row this strip needs (its columns plus 4 on
   // each side, rounded up to whole chunks; never past the stage row)
@@ -677,13 +678,17 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
           };
           if (own) {
             const float2 v = rho2(sx);
+            if (halo) {
+              const float2 h = rho2(hs);
+              r0[hs] = h.x;
+              r1[hs] = h.y;
+            }
             r0[sx] = v.x;
             r1[sx] = v.y;
-          }
-          if (halo) {
-            const float2 v = rho2(hs);
-            r0[hs] = v.x;
-            r1[hs] = v.y;
+          } else if (halo) {
+            const float2 h = rho2(hs);
+            r0[hs] = h.x;
+            r1[hs] = h.y;
           }
         } else {
 #pragma unroll
@@ -722,16 +727,17 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                                  V(rb, rc, s + 1), V(rb, rc, s - 1), tb2, dl2, dg2, k62);
             };
             if (own) {
+              // all loads before the ring stores, so that they are shared
               const float2 mu = at2(sx);
-              m0[sx] = mu.x;
-              m1[sx] = mu.y;
               frs2 = V(rc, ra, sx);
               iso_grad_x2(V(rc, ra, sx + 1), V(rc, ra, sx - 1), V(ra, rt, sx), V(rb, rc, sx),
                           V(ra, rt, sx + 1), V(ra, rt, sx - 1), V(rb, rc, sx + 1),
                           V(rb, rc, sx - 1), fgx2, fgy2);
+              m0[sx] = mu.x;
+              m1[sx] = mu.y;
             }
-            if (tx < 2) {                  // halo mu at slots 3 and w+4
-              const int s = tx == 0 ? 3 : w + 4;
+            if (tx == mu_lo || tx == mu_hi) {   // halo mu at slots 3 and w+4
+              const int s = tx == mu_lo ? 3 : w + 4;
               const float2 mu = at2(s);
               m0[s] = mu.x;
               m1[s] = mu.y;
