@@ -337,6 +337,11 @@ def run_ours(args, world, rank, local):
     peak_note = "of measured" if hbm_peak else "of fallback"
     hbm_peak = hbm_peak or 6800.0
     stream = torch.cuda.Stream(device=dev)
+    if args.only == "batched":
+        # the batched leg alone (a partial run, not the benchmark line)
+        if rank == 0:
+            print(json.dumps({"batched": run_batched(args, stream, torch)}), flush=True)
+        return 0
     results = {}
     precisions = [("f32", wblbe.FP32_SHIFTED), ("f64", wblbe.FP64)]
     if args.only != "both":
@@ -445,7 +450,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", type=int, default=4096,
                     help="lattice side (4096 is the benchmark; smaller sides are for profiling)")
-    ap.add_argument("--only", choices=["both", "f32", "f64"], default="both")
+    ap.add_argument("--only", choices=["both", "f32", "f64", "batched"], default="both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")

@@ -90,7 +90,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 template <typename T, bool WB, int TX>
-__global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
+__global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
     batch_persistent_kernel(const BatchDev d) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ int s_item, s_ok;
@@ -127,7 +127,13 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     __syncthreads();
     if (!s_ok) break;                      // nothing of this CTA is in flight
     const CaseDev& cs = d.cases[tile.c];
-    const KParams kp = cs.kp;
+    // the case's parameters in shared memory: no registers held for them,
+    // and no reloads after the population stores (which could alias
+    // device memory)
+    __shared__ KParams s_kp;
+    if (threadIdx.x == 0) s_kp = cs.kp;
+    __syncthreads();
+    const KParams& kp = s_kp;
     const int cur = (cs.cur + j) & 1;
     const T* src = arena + cs.off[cur];
     T* dst = arena + cs.off[cur ^ 1];
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(128)
 
 // Moments of one case (ghost layout), one CTA per tile of the case's grid.
 template <typename T, bool WB, int TX>
-__global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
+__global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
     batch_case_moments_kernel(const T* __restrict__ pops, const KParams kp,
                               const MomentsOut mo) {
   extern __shared__ __align__(128) unsigned char smem_raw[];

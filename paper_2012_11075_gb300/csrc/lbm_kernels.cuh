@@ -414,12 +414,15 @@ template <> struct Staging<float> {
   static constexpr int kAhead = 2;
   static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 8
   __host__ __device__ static constexpr int min_blocks(int tx) { return 640 / tx > 1 ? 640 / tx : 1; }
+  // kernels that keep per-case parameters in registers (batched)
+  __host__ __device__ static constexpr int min_blocks_batch(int tx) { return 65536 / (tx * 128); }
 };
 template <> struct Staging<double> {
   static constexpr int kRows = 1;
   static constexpr int kAhead = 1;
   static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 4
   __host__ __device__ static constexpr int min_blocks(int tx) { return 65536 / (tx * 128); }
+  __host__ __device__ static constexpr int min_blocks_batch(int tx) { return 65536 / (tx * 128); }
 };
 
 constexpr int kPad = 4;   // staged columns on each side of a strip (x0-4 .. x0+TX+3)
@@ -461,6 +464,63 @@ enum StripMode {
   kModeStepStats = 2   // store, and accumulate per-CTA stats of f(t)
 };
 
+// Per-CTA statistics of the collided nodes (FP64 accumulators).
+struct StatsAcc {
+  double mass = 0.0, kin = 0.0, u2 = 0.0, mumin = 1e300, mumax = -1e300;
+  int bad = 0;
+};
+
+// One collided node of row c: store its nine populations (and the ghost
+// copies of a boundary column), or write its moment fields, and fold its
+// statistics.  Forced inline so that the population array stays in registers.
+template <typename T, int MODE, bool GHOST>
+__device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo, T* dst, int c,
+                                          int xcol, int xm, bool ghost_r, bool ghost_l,
+                                          const T (&gv)[9], T rs, T muc, T ux, T uy,
+                                          StatsAcc& acc, bool acc_on) {
+  constexpr bool MOMENTS = MODE == kModeMoments;
+  constexpr bool STATS = MODE != kModeStep;
+  if (!MOMENTS) {
+    if (GHOST) {
+      // parameters live in shared memory here: one running pointer
+      T* o = dst + (unsigned)(c * p.pitch + xcol);
+      const long long pl = p.plane;
+      const int nx = p.nx;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        *o = gv[i];
+        if (ghost_r) o[nx] = gv[i];
+        if (ghost_l) o[-nx] = gv[i];
+        o += pl;
+      }
+    } else {
+      // kernel parameters: per-plane bases and one 32-bit offset
+      const unsigned off = (unsigned)(c * p.pitch + xcol);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) (dst + i * p.plane)[off] = gv[i];
+    }
+  }
+  if (STATS && acc_on) {
+    const double rho = (double)rs + p.rho_ref;
+    const double mu = (double)muc;
+    const double dux = (double)ux, duy = (double)uy;
+    if (MOMENTS) {
+      const unsigned kk = (unsigned)(c * p.nx + xm);
+      if (mo.rho) mo.rho[kk] = rho;
+      if (mo.ux) mo.ux[kk] = dux;
+      if (mo.uy) mo.uy[kk] = duy;
+      if (mo.mu) mo.mu[kk] = mu;
+    }
+    const double u2 = dux * dux + duy * duy;
+    acc.mass += rho;
+    acc.kin += 0.5 * rho * u2;
+    acc.u2 = fmax(acc.u2, u2);
+    acc.mumin = fmin(acc.mumin, mu);
+    acc.mumax = fmax(acc.mumax, mu);
+    if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) acc.bad = 1;
+  }
+}
+
 // GHOST selects the row layout with ghost columns used by the batched
 // kernel: column x of a row is stored at x + 4 and the four columns on each
 // side hold copies of the wrapped columns (x = -4..-1 -> nx-4..nx-1,
@@ -475,7 +535,6 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                                            const KParams& p, const MomentsOut& mo, int x0,
                                            int y0, int y1, double* stats_rec,
                                            unsigned char* smem_raw) {
-  constexpr bool MOMENTS = MODE == kModeMoments;
   constexpr bool STATS = MODE != kModeStep;
   constexpr int R = Staging<T>::kRows;     // rows per iteration
   constexpr int PDG = Staging<T>::kAhead;  // row groups requested ahead of use
@@ -580,9 +639,6 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
            st[8 * SW + s - 1];
   };
 
-  double st_mass = 0.0, st_kin = 0.0, st_u2 = 0.0;
-  double st_mumin = 1e300, st_mumax = -1e300;
-  int st_bad = 0;
 
   // Rows kfirst .. kfirst + nlast are processed in groups of R (a row past
   // klast only feeds values nobody reads).
@@ -610,38 +666,11 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   cp_async_wait<PDG - 1>();                // first group landed (this thread)
   __syncthreads();                         // ... and everyone else's
 
-  // One collided node: store (or write the moment fields) and fold the stats.
-  auto emit = [&](int c, const T (&gv)[9], T rs, T muc, T ux, T uy) {
-    if (!MOMENTS) {
-      const unsigned off = (unsigned)(c * p.pitch + xcol);
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        T* di = dst + i * p.plane;
-        di[off] = gv[i];
-        if (ghost_r) di[off + p.nx] = gv[i];
-        if (ghost_l) di[off - p.nx] = gv[i];
-      }
-    }
-    if (STATS) {
-      const double rho = (double)rs + p.rho_ref;
-      const double mu = (double)muc;
-      const double dux = (double)ux, duy = (double)uy;
-      if (MOMENTS) {
-        const unsigned kk = (unsigned)(c * p.nx + x0 + tx);
-        if (mo.rho) mo.rho[kk] = rho;
-        if (mo.ux) mo.ux[kk] = dux;
-        if (mo.uy) mo.uy[kk] = duy;
-        if (mo.mu) mo.mu[kk] = mu;
-      }
-      const double u2 = dux * dux + duy * duy;
-      st_mass += rho;
-      st_kin += 0.5 * rho * u2;
-      st_u2 = fmax(st_u2, u2);
-      st_mumin = fmin(st_mumin, mu);
-      st_mumax = fmax(st_mumax, mu);
-      if (!isfinite(rho) || !isfinite(mu) || !isfinite(u2)) st_bad = 1;
-    }
-  };
+  StatsAcc acc;
+  const int xm = x0 + tx;                  // column of the moment fields
+  // statistics are gathered only into a record (a uniform, runtime choice in
+  // the step-and-statistics mode, so that one instantiation serves both)
+  const bool acc_on = MODE == kModeMoments || stats_rec != nullptr;
 
   // FP32: the two rows of an iteration run as float2 pairs
   constexpr bool kPacked = sizeof(T) == 4 && R == 2;
@@ -797,12 +826,14 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
             if (v0) {
               const T gl[9] = {g[0].x, g[1].x, g[2].x, g[3].x, g[4].x,
                                g[5].x, g[6].x, g[7].x, g[8].x};
-              emit(c0, gl, rs.x, STATS ? mB[sx] : T(0), ux.x, uy.x);
+              emit_node<T, MODE, GHOST>(p, mo, dst, c0, xcol, xm, ghost_r, ghost_l, gl, rs.x,
+                                        STATS ? mB[sx] : T(0), ux.x, uy.x, acc, acc_on);
             }
             if (v1) {
               const T gh[9] = {g[0].y, g[1].y, g[2].y, g[3].y, g[4].y,
                                g[5].y, g[6].y, g[7].y, g[8].y};
-              emit(c0 + 1, gh, rs.y, STATS ? mC[sx] : T(0), ux.y, uy.y);
+              emit_node<T, MODE, GHOST>(p, mo, dst, c0 + 1, xcol, xm, ghost_r, ghost_l, gh,
+                                        rs.y, STATS ? mC[sx] : T(0), ux.y, uy.y, acc, acc_on);
             }
           }
           prs2 = frs2;
@@ -830,7 +861,8 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                         st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
               T ux, uy;
               collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
-              emit(c, g, rs, STATS ? m_c[sx] : T(0), ux, uy);
+              emit_node<T, MODE, GHOST>(p, mo, dst, c, xcol, xm, ghost_r, ghost_l, g, rs,
+                                        STATS ? m_c[sx] : T(0), ux, uy, acc, acc_on);
             }
           }
           prs = frs[R - 1];
@@ -846,7 +878,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   if (STATS && stats_rec) {
     // deterministic block reduction: warp shuffle, then thread 0 over warps
     __shared__ double red[kMaxTile / 32][kStatRec];
-    double v[kStatRec] = {st_mass, st_kin, st_u2, st_mumin, st_mumax, (double)st_bad};
+    double v[kStatRec] = {acc.mass, acc.kin, acc.u2, acc.mumin, acc.mumax, (double)acc.bad};
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       double o0 = __shfl_down_sync(0xffffffffu, v[0], off);
