@@ -249,13 +249,16 @@ def test_lattice_symmetry_equivariance(scheme):
 
 # ---- the discrete equilibrium state S = {mu = const, u = 0} (Sec. I, III) ---------
 
-def test_well_balanced_flat_interface_reaches_discrete_equilibrium():
+@pytest.mark.parametrize("rho0", [0.0, 0.1, 0.55])
+def test_well_balanced_flat_interface_reaches_discrete_equilibrium(rho0):
     """A WB run from the tanh profile converges to the fixed-mass solution of
     mu_0(rho_j) - kappa lap_h rho_j = const found by Newton's method without
     the LBE.  Odd lattice: on even ones the balance of Sec. III also admits
-    an alternating mode rho_j d_h mu_j = a (-1)^j."""
+    an alternating mode rho_j d_h mu_j = a (-1)^j.  The constant rho0 of
+    Eq. mFeq (0, rho_g, the mean density) does not change that state: the
+    balance of Sec. III does not contain it."""
     ny = 21
-    p = _params(nx=1, ny=ny, scheme=WELL_BALANCED, tau=0.8)
+    p = _params(nx=1, ny=ny, scheme=WELL_BALANCED, tau=0.8, rho0=rho0)
     rho_init = _slab(ny)[:, None].copy()
     o = Oracle(p)
     f = o.init(rho_init)
