@@ -1,0 +1,94 @@
+"""The constant rho0 of the well-balanced equilibrium on the GPU (Sec. III):
+it leaves the equilibrium state unchanged, and the stability map over
+(rho0, density ratio, tau) runs through the batched kernel.  Host-side table
+formatting is checked on the CPU."""
+import numpy as np
+import pytest
+
+from paper_2012_11075_gb300 import stability
+
+
+def test_rho0_values_and_table_layout():
+    assert stability.rho0_value("zero", 1.0, 0.1) == 0.0
+    assert stability.rho0_value("gas", 1.0, 0.1) == 0.1
+    assert stability.rho0_value("mean", 1.0, 0.1) == pytest.approx(0.55)
+    with pytest.raises(ValueError):
+        stability.rho0_value("liquid", 1.0, 0.1)
+    recs = [{"rho0_mode": m, "ratio": q, "tau": t, "state": s, "steps": 500, "umax": 1e-6}
+            for m in ("zero", "gas") for q in (2.0, 10.0) for t in (0.6, 1.0)
+            for s in (["unstable"] if (q == 10.0 and t == 0.6) else ["stable"])]
+    txt = stability.format_table(recs)
+    assert txt.count("rho0 =") == 2 and txt.count("x@500") == 2
+    assert len(stability.grid((2, 10), (0.6, 1.0))) == 3 * 2 * 2
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("rho0", [0.1, 0.55])
+def test_equilibrium_does_not_depend_on_rho0_on_gpu(rho0):
+    """FP64 WB slab (1 x 21, tau = 0.8) run to max|u| < 1e-13 and 50000 steps
+    with rho0 = rho_g and the mean density: the density is the Newton
+    solution of the discrete equilibrium (which has no rho0), to 1e-10."""
+    from tests.gpu_helpers import gpu_params, need_gpu
+    need_gpu()
+    from oracle import equilibrium as eq
+    from paper_2012_11075_gb300 import wblbe
+    from paper_2012_11075_gb300 import workloads as wl
+    ny = 21
+    y = np.arange(ny, dtype=float)
+    d = np.minimum(y, ny - y)
+    prof = 0.55 + 0.45 * np.tanh(2 * (d - ny / 4) / 4.0)
+    beta = wl.beta_for_width(0.01, 4.0, 1.0, 0.1)
+    pr = wl.Problem(1, ny, 0.8, 0.01, beta, 1.0, 0.1, prof[:, None].copy())
+    s = wblbe.Solver(gpu_params(pr, wblbe.WELL_BALANCED, rho0=rho0))
+    s.init_rho(pr.rho)
+    code, done, st = s.run_until_equilibrium(1e-13, 200000, 1000)
+    assert code == wblbe.OK and st["umax"] < 1e-13
+    s.step(50000 - done if done < 50000 else 0)
+    m, st = s.moments()
+    s.close()
+    rN, _ = eq.discrete_flat_equilibrium(prof, 0.01, beta, 1.0, 0.1)
+    assert st["mu_max"] - st["mu_min"] < 1e-13
+    assert np.max(np.abs(m["rho"][:, 0] - rN)) < 1e-10
+
+
+@pytest.mark.gpu
+def test_small_stability_map_runs_every_case():
+    """A 2 x 2 x 3 map (ratio 2 and 10, tau 0.6 and 1.0, three rho0 choices)
+    on 64^2 droplets for 2000 steps: every case ends stable or unstable with
+    its step count, and the mild corner (ratio 2, tau 1.0) is stable with a
+    small spurious velocity for every rho0."""
+    from tests.gpu_helpers import need_gpu
+    need_gpu()
+    recs = stability.stability_map(ratios=(2.0, 10.0), taus=(0.6, 1.0), n=64, steps=2000,
+                                   steps_per_launch=50)
+    assert len(recs) == 12
+    for r in recs:
+        assert r["state"] in ("stable", "unstable")
+        if r["state"] == "stable":
+            assert r["steps"] == 2000 and np.isfinite(r["umax"])
+        else:
+            assert 0 < r["steps"] <= 2000
+    for r in recs:
+        if r["ratio"] == 2.0 and r["tau"] == 1.0:
+            assert r["state"] == "stable" and r["umax"] < 1e-3, r
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rho0_is_an_exact_offset_on_gpu(precision):
+    """On the GPU, as on the oracle, the WB state with rho0 = 0.3 equals the
+    rho0 = 0 state plus the constant vector b = rho0 (-(1-w0), w_1..w_8)
+    after 1000 steps of the 256^2 droplet: the periodic dynamics do not see
+    rho0 (FP64 to 1e-12; FP32-shifted to its storage rounding)."""
+    from tests.gpu_helpers import need_gpu, run_gpu
+    need_gpu()
+    from paper_2012_11075_gb300 import wblbe
+    from paper_2012_11075_gb300 import workloads as wl
+    prec = wblbe.FP64 if precision == "fp64" else wblbe.FP32_SHIFTED
+    pr = wl.droplet(n=256, radius=40.0, tau=1.0)
+    f0, _, _ = run_gpu(pr, wblbe.WELL_BALANCED, 1000, precision=prec, rho0=0.0)
+    f3, _, _ = run_gpu(pr, wblbe.WELL_BALANCED, 1000, precision=prec, rho0=0.3)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    b = np.concatenate([[-(1 - w[0]) * 0.3], w[1:] * 0.3])
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert np.max(np.abs(f3 - f0 - b[:, None, None])) < tol
