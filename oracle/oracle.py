@@ -27,6 +27,8 @@ HERE = Path(__file__).resolve().parent
 SRC = HERE / "wblbe_oracle.c"
 BUILD_DIR = HERE / "_build"
 LIB_PATH = BUILD_DIR / f"liboracle_{platform.machine()}.so"
+# timing-only build with the row loops split over threads (same arithmetic)
+LIB_OMP_PATH = BUILD_DIR / f"liboracle_omp_{platform.machine()}.so"
 
 STANDARD = 0
 WELL_BALANCED = 1
@@ -38,16 +40,20 @@ CY = (0, 0, 1, 0, -1, 1, 1, -1, -1)
 W = (4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36)
 
 
-def build(force: bool = False) -> Path:
-    """Compile the C oracle (plain gcc, no FMA contraction) if needed."""
+def build(force: bool = False, openmp: bool = False) -> Path:
+    """Compile the C oracle (plain gcc, no FMA contraction) if needed.
+    ``openmp`` builds the timing-only variant whose row loops run on all
+    host threads; every node is computed as in the serial build."""
     BUILD_DIR.mkdir(exist_ok=True)
-    if force or not LIB_PATH.exists() or LIB_PATH.stat().st_mtime < SRC.stat().st_mtime:
-        tmp = LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
+    path = LIB_OMP_PATH if openmp else LIB_PATH
+    if force or not path.exists() or path.stat().st_mtime < SRC.stat().st_mtime:
+        tmp = path.with_suffix(f".{os.getpid()}.tmp")
         subprocess.check_call(
             ["gcc", "-O3", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+             *(["-fopenmp"] if openmp else []),
              "-fPIC", "-shared", "-o", str(tmp), str(SRC), "-lm"])
-        os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+        os.replace(tmp, path)
+    return path
 
 
 class _Params(ctypes.Structure):
@@ -64,13 +70,12 @@ class _Stats(ctypes.Structure):
                 ("kinetic", ctypes.c_double), ("nonfinite", ctypes.c_int)]
 
 
-_lib = None
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(str(build()))
+def _load(openmp: bool = False):
+    if openmp not in _libs:
+        lib = ctypes.CDLL(str(build(openmp=openmp)))
         dp = ctypes.POINTER(ctypes.c_double)
         pp = ctypes.POINTER(_Params)
         for name in ("orc_psi0", "orc_mu0", "orc_p0"):
@@ -86,8 +91,8 @@ def _load():
         lib.orc_step.argtypes = [pp, dp, ctypes.c_long]
         lib.orc_step.restype = ctypes.c_int
         lib.orc_stats_of.argtypes = [pp, dp, ctypes.POINTER(_Stats)]
-        _lib = lib
-    return _lib
+        _libs[openmp] = lib
+    return _libs[openmp]
 
 
 def _ptr(a: np.ndarray):
@@ -118,10 +123,12 @@ class Params:
 class Oracle:
     """FP64 CPU oracle bound to one parameter set."""
 
-    def __init__(self, params: Params):
+    def __init__(self, params: Params, openmp: bool = False):
+        """``openmp``: use the timing build whose loops run on all host
+        threads (for the benchmark's all-cores baseline); same results."""
         self.p = params
         self._cp = params._c()
-        self._lib = _load()
+        self._lib = _load(openmp)
 
     # -- free energy (Eq. doubleWell, Eq. EOS) --------------------------------
     def psi0(self, rho: float) -> float:

@@ -388,3 +388,22 @@ def test_rho0_is_an_exact_offset_on_periodic_lattices():
     # 500 steps; a missing or wrong rho0 term would show at O(rho0 w_i)
     assert np.max(np.abs(diff - b[:, None, None])) < 1e-12
     assert np.max(np.abs(out[0.0][1:] - np.mean(out[0.0][1:]))) > 1e-6   # the run is not trivial
+
+
+def test_threaded_timing_build_is_bitwise_identical():
+    """The all-cores timing build of the oracle (row loops split over threads
+    with OpenMP) computes every node as the serial build does: identical
+    bits after 50 steps of a noisy droplet with several threads."""
+    import os
+    os.environ.setdefault("OMP_NUM_THREADS", "4")
+    p = _params(nx=40, ny=37, scheme=WELL_BALANCED, tau=1.0)
+    rho = _slab(37)[:, None] * np.ones((1, 40))
+    rho = rho + 0.01 * np.random.default_rng(3).uniform(-1, 1, rho.shape)
+    out = []
+    for omp in (False, True):
+        o = Oracle(p, openmp=omp)
+        f = o.init(rho.copy())
+        o.step(f, 50)
+        out.append(f)
+    assert np.all(np.isfinite(out[0]))
+    assert np.array_equal(out[0], out[1])
