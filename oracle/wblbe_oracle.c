@@ -50,7 +50,12 @@ static const double WQ[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
 
-enum { ORC_STANDARD = 0, ORC_WELL_BALANCED = 1 };
+/* Schemes: the standard LBE of Sec. II (potential-form force, Eq. Fi), the
+ * well-balanced LBE of Sec. III, and two variants of the standard LBE that
+ * Sec. II compares it with: the pressure-form force, and the forcing term of
+ * Guo's textbook, F_i = (c_i - u).F f_i^eq / (cs^2 rho). */
+enum { ORC_STANDARD = 0, ORC_WELL_BALANCED = 1, ORC_STANDARD_PRESSURE = 2,
+       ORC_STANDARD_GUO = 3 };
 
 /* Problem statement (Sec. IV): lattice, relaxation time, free-energy
  * parameters, the WB constant rho0 (Eq. mFeq) and the scheme. */
@@ -188,6 +193,19 @@ static void forcing_well_balanced(double ux, double uy, double Fx, double Fy,
   }
 }
 
+/* Forcing term of Guo's textbook quoted in Sec. II:
+ * F_i = (c_i - u).F f_i^eq / (cs^2 rho), with the standard equilibrium; the
+ * density cancels, f_i^eq / rho being the standard equilibrium at rho = 1. */
+static void forcing_guo_book(double ux, double uy, double Fx, double Fy,
+                             double* Fi) {
+  double feq1[Q];
+  feq_standard(1.0, ux, uy, feq1);
+  for (int i = 0; i < Q; ++i) {
+    double cuF = (CX[i] - ux) * Fx + (CY[i] - uy) * Fy;
+    Fi[i] = cuF * feq1[i] / CS2;
+  }
+}
+
 void orc_feq(const orc_params* p, double rho, double ux, double uy,
              double* feq) {
   if (p->scheme == ORC_WELL_BALANCED)
@@ -200,6 +218,8 @@ void orc_forcing(const orc_params* p, double ux, double uy, double Fx,
                  double Fy, double grx, double gry, double* Fi) {
   if (p->scheme == ORC_WELL_BALANCED)
     forcing_well_balanced(ux, uy, Fx, Fy, grx, gry, Fi);
+  else if (p->scheme == ORC_STANDARD_GUO)
+    forcing_guo_book(ux, uy, Fx, Fy, Fi);
   else
     forcing_standard(ux, uy, Fx, Fy, Fi);
 }
@@ -211,6 +231,12 @@ void orc_forcing(const orc_params* p, double ux, double uy, double Fx,
  *   mu  = mu_0(rho) - kappa lap(rho)                 (Sec. II)
  *   F   = -rho grad(mu)                 (WB, Eq. mF)
  *       = grad(cs^2 rho) - rho grad(mu) (standard, potential form, Sec. II)
+ *       = grad(cs^2 rho - p_0) + kappa rho grad(lap(rho))
+ *                                       (standard, pressure form, Sec. II)
+ * The pressure form is printed with "- kappa grad(lap rho)"; the paper calls
+ * the two forms identical, which holds only with "+ kappa rho grad(lap rho)"
+ * (rho grad mu = grad p_0 - kappa rho grad lap rho, from p_0 = rho mu_0 -
+ * psi_0): that is the reading taken.
  *   u   = (sum_i c_i f_i + F/2) / rho                (Eq. rhoU)
  * Any output pointer may be NULL. */
 void orc_macro(const orc_params* p, const double* f, double* rho_out,
@@ -236,6 +262,19 @@ void orc_macro(const orc_params* p, const double* f, double* rho_out,
   for (size_t k = 0; k < n; ++k) mu[k] = orc_mu0(p, rho[k]) - p->kappa * lap[k];
   orc_gradient(p, mu, gmx, gmy);
   orc_gradient(p, rho, grx, gry);
+  /* pressure form: gmx/gmy become grad(lap rho), and gAx/gAy the gradient of
+   * A = cs^2 rho - p_0(rho) */
+  double* gAx = NULL;
+  double* gAy = NULL;
+  if (p->scheme == ORC_STANDARD_PRESSURE) {
+    double* A = (double*)malloc(n * sizeof(double));
+    gAx = (double*)malloc(n * sizeof(double));
+    gAy = (double*)malloc(n * sizeof(double));
+    for (size_t k = 0; k < n; ++k) A[k] = CS2 * rho[k] - orc_p0(p, rho[k]);
+    orc_gradient(p, A, gAx, gAy);
+    orc_gradient(p, lap, gmx, gmy);
+    free(A);
+  }
 
 #pragma omp parallel for
   for (size_t k = 0; k < n; ++k) {
@@ -243,6 +282,9 @@ void orc_macro(const orc_params* p, const double* f, double* rho_out,
     if (p->scheme == ORC_WELL_BALANCED) {
       Fx = -rho[k] * gmx[k];
       Fy = -rho[k] * gmy[k];
+    } else if (p->scheme == ORC_STANDARD_PRESSURE) {
+      Fx = gAx[k] + p->kappa * rho[k] * gmx[k];
+      Fy = gAy[k] + p->kappa * rho[k] * gmy[k];
     } else {
       Fx = CS2 * grx[k] - rho[k] * gmx[k];
       Fy = CS2 * gry[k] - rho[k] * gmy[k];
@@ -262,6 +304,7 @@ void orc_macro(const orc_params* p, const double* f, double* rho_out,
     if (gry_out) gry_out[k] = gry[k];
   }
   free(rho); free(lap); free(mu); free(gmx); free(gmy); free(grx); free(gry);
+  free(gAx); free(gAy);
 }
 
 /* ---- Initial state ------------------------------------------------------ */

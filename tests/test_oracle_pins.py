@@ -407,3 +407,67 @@ def test_threaded_timing_build_is_bitwise_identical():
         out.append(f)
     assert np.all(np.isfinite(out[0]))
     assert np.array_equal(out[0], out[1])
+
+
+# ---- the comparison variants of the standard LBE (Sec. II) -------------------
+
+def test_pressure_form_matches_potential_form():
+    """The pressure-form force grad(cs^2 rho - p_0) + kappa rho grad(lap rho)
+    and the potential form grad(cs^2 rho) - rho grad(mu) are equal in the
+    continuum (p_0 = rho mu_0 - psi_0).  The discrete gradient is linear, so
+    their difference is rho grad(mu_0) - grad(p_0) node by node: the kappa
+    parts cancel exactly (the difference does not change when kappa does),
+    and what is left is a second-order truncation error (halving the
+    spacing divides it by about 4)."""
+    from oracle.oracle import STANDARD_PRESSURE
+
+    def forces(L, kappa, beta):
+        x = np.arange(L)[None, :]
+        y = np.arange(L)[:, None]
+        rho = 0.55 + 0.3 * np.sin(2 * np.pi * x / L) * np.cos(2 * np.pi * y / L)
+        out = {}
+        for sch in (STANDARD, STANDARD_PRESSURE):
+            o = Oracle(_params(nx=L, ny=L, scheme=sch, tau=1.0, kappa=kappa, beta=beta))
+            m = o.macro(o.init(rho))
+            out[sch] = np.stack([m["Fx"], m["Fy"]])
+        o = Oracle(_params(nx=L, ny=L, scheme=STANDARD, tau=1.0, kappa=0.0, beta=beta))
+        m = o.macro(o.init(rho))
+        nonideal = np.stack([m["Fx"], m["Fy"]]) - np.stack(o.gradient(rho)) / 3.0
+        return out[STANDARD_PRESSURE] - out[STANDARD], np.abs(nonideal).max()
+
+    beta = 0.006
+    d1, _ = forces(48, 0.01, beta)
+    d2, _ = forces(48, 0.04, beta)
+    assert np.abs(d1 - d2).max() < 1e-15          # kappa terms cancel
+    errs = []
+    for L in (32, 64, 128):
+        d, scale = forces(L, 0.01, beta)
+        errs.append(np.abs(d).max() / scale)
+    assert errs[0] < 0.05
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_textbook_forcing_moments():
+    """Guo's textbook forcing F_i = (c_i - u).F f_i^eq/(cs^2 rho): sum F_i = 0,
+    sum c_i F_i = F, and sum c_a c_b F_i = u_a F_b + F_a u_b
+    - u_a u_b (u.F)/cs^2 (from the D2Q9 moments of f^eq); it matches the
+    second moment of Eq. Fi up to that O(u^3) term."""
+    from oracle.oracle import CX, CY, STANDARD_GUO
+    o = Oracle(_params(scheme=STANDARD_GUO))
+    os_ = Oracle(_params(scheme=STANDARD))
+    rng = np.random.default_rng(11)
+    cx, cy = np.array(CX, float), np.array(CY, float)
+    for _ in range(20):
+        ux, uy, Fx, Fy = rng.uniform(-0.1, 0.1, 4)
+        Fi = o.forcing(ux, uy, Fx, Fy)
+        assert abs(Fi.sum()) < 1e-16
+        assert abs((cx * Fi).sum() - Fx) < 1e-16 and abs((cy * Fi).sum() - Fy) < 1e-16
+        uF = ux * Fx + uy * Fy
+        m2 = {(a, b): (ca * cb * Fi).sum() for a, ca in (("x", cx), ("y", cy))
+              for b, cb in (("x", cx), ("y", cy))}
+        u = {"x": ux, "y": uy}
+        F = {"x": Fx, "y": Fy}
+        for (a, b), v in m2.items():
+            assert abs(v - (u[a] * F[b] + F[a] * u[b] - 3.0 * u[a] * u[b] * uF)) < 1e-16
+        Fs = os_.forcing(ux, uy, Fx, Fy)
+        assert abs((cx * cx * (Fi - Fs)).sum() + 3.0 * ux * ux * uF) < 1e-16
