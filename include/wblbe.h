@@ -58,8 +58,19 @@ typedef enum {
   WBLBE_ENOTCONVERGED = 6  /* max_steps reached; the state is still valid   */
 } wblbe_status;
 
-/* Scheme: the standard LBE of Sec. II or the well-balanced LBE of Sec. III. */
-enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1 };
+/* Scheme: the standard LBE of Sec. II (potential-form force, forcing term
+ * Eq. Fi) or the well-balanced LBE of Sec. III; and two variants of the
+ * standard LBE that Sec. II compares with, for single lattices only (the
+ * batch API rejects them with WBLBE_EINVAL):
+ *   WBLBE_STANDARD_PRESSURE: pressure-form force
+ *     F = grad(cs^2 rho - p_0) + kappa rho grad(lap rho) (Sec. II; the paper
+ *     prints "- kappa grad(lap rho)", which would not equal the potential
+ *     form it is said to equal);
+ *   WBLBE_STANDARD_TEXTBOOK: potential-form force with the forcing term of
+ *     Guo's textbook quoted in Sec. II, F_i = (c_i - u).F f_i^eq/(cs^2 rho).
+ * Both use the standard equilibrium Eq. feq (and its FP32 shift). */
+enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1, WBLBE_STANDARD_PRESSURE = 2,
+       WBLBE_STANDARD_TEXTBOOK = 3 };
 
 /* Storage/arithmetic precision.
  * WBLBE_FP64: populations stored and updated in float64.
@@ -82,7 +93,7 @@ typedef struct {
   double tau, kappa, beta, rho_l, rho_g;
   double rho0;
   double rho_ref;
-  int32_t scheme;     /* WBLBE_STANDARD | WBLBE_WELL_BALANCED   */
+  int32_t scheme;     /* WBLBE_STANDARD .. WBLBE_STANDARD_TEXTBOOK */
   int32_t precision;  /* WBLBE_FP64 | WBLBE_FP32_SHIFTED        */
 } wblbe_params;
 

@@ -34,7 +34,7 @@ STANDARD = 0
 WELL_BALANCED = 1
 # variants of the standard LBE compared in Sec. II
 STANDARD_PRESSURE = 2      # pressure-form interaction force
-STANDARD_GUO = 3           # forcing term of Guo's textbook
+STANDARD_TEXTBOOK = 3           # forcing term of Guo's textbook
 
 # D2Q9 velocity set and weights as the paper states them (Sec. II), kept here
 # for tests that need to name a direction.

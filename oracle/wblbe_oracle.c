@@ -55,7 +55,7 @@ static const double CS2 = 1.0 / 3.0;
  * Sec. II compares it with: the pressure-form force, and the forcing term of
  * Guo's textbook, F_i = (c_i - u).F f_i^eq / (cs^2 rho). */
 enum { ORC_STANDARD = 0, ORC_WELL_BALANCED = 1, ORC_STANDARD_PRESSURE = 2,
-       ORC_STANDARD_GUO = 3 };
+       ORC_STANDARD_TEXTBOOK = 3 };
 
 /* Problem statement (Sec. IV): lattice, relaxation time, free-energy
  * parameters, the WB constant rho0 (Eq. mFeq) and the scheme. */
@@ -218,7 +218,7 @@ void orc_forcing(const orc_params* p, double ux, double uy, double Fx,
                  double Fy, double grx, double gry, double* Fi) {
   if (p->scheme == ORC_WELL_BALANCED)
     forcing_well_balanced(ux, uy, Fx, Fy, grx, gry, Fi);
-  else if (p->scheme == ORC_STANDARD_GUO)
+  else if (p->scheme == ORC_STANDARD_TEXTBOOK)
     forcing_guo_book(ux, uy, Fx, Fy, Fi);
   else
     forcing_standard(ux, uy, Fx, Fy, Fi);

@@ -15,13 +15,15 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 LIB_DIR = PKG / "_lib"
 LIB_PATH = LIB_DIR / f"libwblbe_{platform.machine()}.so"
-SOURCES = [CSRC / "wblbe.cu", CSRC / "batch.cu", CSRC / "wblbe_noalloc.cu"]
-DEPENDS = SOURCES + [CSRC / "lbm_kernels.cuh", ROOT / "include" / "wblbe.h"]
+SOURCES = [CSRC / "batch.cu", CSRC / "wblbe.cu", CSRC / "strip_variants.cu",
+           CSRC / "wblbe_noalloc.cu"]
+DEPENDS = SOURCES + [CSRC / "lbm_kernels.cuh", CSRC / "strip_launch.cuh",
+                     ROOT / "include" / "wblbe.h"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
     "--expt-relaxed-constexpr",
 ]
 
@@ -42,11 +44,30 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> Path:
     """Compile libwblbe.so if it is missing or older than its sources."""
     if not force and not needs_build():
         return LIB_PATH
+    from concurrent.futures import ThreadPoolExecutor
     LIB_DIR.mkdir(exist_ok=True)
-    tmp = LIB_PATH.with_suffix(f".{os.getpid()}.tmp")
-    cmd = [nvcc(), *NVCC_FLAGS, *extra_flags, "-o", str(tmp), *map(str, SOURCES)]
+    obj_dir = LIB_DIR / f"obj_{platform.machine()}"
+    obj_dir.mkdir(exist_ok=True)
+    tag = os.getpid()
+    objs = [obj_dir / f"{src.stem}.{tag}.o" for src in SOURCES]
+
+    def compile_one(src, obj):
+        cmd = [nvcc(), *NVCC_FLAGS, *extra_flags, "-c", "-o", str(obj), str(src)]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        subprocess.check_call(cmd)
+
+    # the translation units compile in parallel, then one link
+    with ThreadPoolExecutor(len(SOURCES)) as ex:
+        for j in [ex.submit(compile_one, s, o) for s, o in zip(SOURCES, objs)]:
+            j.result()
+    tmp = LIB_PATH.with_suffix(f".{tag}.tmp")
+    cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+           "-o", str(tmp), *map(str, objs)]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
+    for o in objs:
+        o.unlink()
     os.replace(tmp, LIB_PATH)
     return LIB_PATH

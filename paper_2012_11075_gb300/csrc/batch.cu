@@ -138,12 +138,13 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
     const T* src = arena + cs.off[cur];
     T* dst = arena + cs.off[cur ^ 1];
     const MomentsOut mo{};
+    constexpr int SCH = WB ? kSchWB : kSchStandard;
     if (j == K - 1)
-      strip_pass<T, WB, kModeStepStats, TX, true>(src, dst, kp, mo, tile.x0, tile.y0, tile.y1,
-                                                  d.tile_stats + (size_t)t * kStatRec, smem_raw);
+      strip_pass<T, SCH, kModeStepStats, TX, true>(src, dst, kp, mo, tile.x0, tile.y0, tile.y1,
+                                                   d.tile_stats + (size_t)t * kStatRec, smem_raw);
     else
-      strip_pass<T, WB, kModeStep, TX, true>(src, dst, kp, mo, tile.x0, tile.y0, tile.y1,
-                                             nullptr, smem_raw);
+      strip_pass<T, SCH, kModeStep, TX, true>(src, dst, kp, mo, tile.x0, tile.y0, tile.y1,
+                                              nullptr, smem_raw);
     __threadfence();                       // this thread's stores, device-wide
     __syncthreads();
     if (threadIdx.x == 0) st_release(d.done + t, j + 1);
@@ -207,7 +208,8 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
   const int y0 = blockIdx.y * kp.rows;
   const int y1 = min(y0 + kp.rows, kp.ny);
   double* rec = mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec;
-  strip_pass<T, WB, kModeMoments, TX, true>(pops, nullptr, kp, mo, x0, y0, y1, rec, smem_raw);
+  constexpr int SCH = WB ? kSchWB : kSchStandard;
+  strip_pass<T, SCH, kModeMoments, TX, true>(pops, nullptr, kp, mo, x0, y0, y1, rec, smem_raw);
 }
 
 // Initial state of one case in the ghost layout: P_i(x) = f_i^eq(rho(x+c_i), 0)
@@ -743,7 +745,9 @@ wblbe_status wblbe_batch_create(int32_t scheme, int32_t precision, int32_t max_c
   if (!out) return bfail(nullptr, WBLBE_EINVAL, "out is NULL");
   *out = nullptr;
   if (scheme != WBLBE_STANDARD && scheme != WBLBE_WELL_BALANCED)
-    return bfail(nullptr, WBLBE_EINVAL, "unknown scheme");
+    return bfail(nullptr, WBLBE_EINVAL,
+                 "the batch runs the standard and well-balanced schemes only "
+                 "(the comparison variants run on single lattices)");
   if (precision != WBLBE_FP64 && precision != WBLBE_FP32_SHIFTED)
     return bfail(nullptr, WBLBE_EINVAL, "unknown precision");
   if (max_cases < 1 || max_tiles < 1 || max_case_nodes < 64)

@@ -58,6 +58,13 @@ struct MomentsOut {
 
 constexpr int kStatRec = 6;       // mass, kinetic, umax^2, mu_min, mu_max, nonfinite
 
+// Schemes (the values of the C ABI's scheme codes): the standard LBE of
+// Sec. II (potential-form force, Eq. Fi), the well-balanced LBE of Sec. III,
+// and two variants of the standard LBE that Sec. II compares: the
+// pressure-form force grad(cs^2 rho - p_0) + kappa rho grad(lap rho), and the
+// forcing term F_i = (c_i - u).F f_i^eq / (cs^2 rho) of Guo's textbook.
+enum SchemeId : int { kSchStandard = 0, kSchWB = 1, kSchPressure = 2, kSchTextbook = 3 };
+
 __device__ __forceinline__ int wrap_index(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -97,9 +104,9 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // 1 - omega is exact (Sterbenz); for smaller omega, omega is taken as 1 - keep.
 template <typename T>
 struct CollideConsts {
-  T omega, kf, keep, kf_m3, rho_ref, wb_b0c, om_bax, om_bdg;
+  T omega, kf, keep, kf_m3, rho_ref, wb_b0c, om_bax, om_bdg, kappa;
   __device__ explicit CollideConsts(const KParams& p)
-      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)),
+      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)),
         wb_b0c(T(p.wb_b0c)), om_bax(T(p.omega * p.wb_bax)), om_bdg(T(p.omega * p.wb_bdg)) {
     const T w = T(p.omega);
     if (w >= T(0.5)) {
@@ -128,10 +135,18 @@ struct CollideConsts {
 // kforce (-3 u.G) and k_u = kforce (u.grad rho):
 //   E_0 = w_0 (t - k_u) + omega b_0,   E_axis base = w_ax (t + k_u/2) + omega b_ax,
 //   E_diag base = w_dg (t + 2 k_u) + omega b_dg.
-template <typename T, bool WB>
+// The variants of the standard scheme: with the pressure form the gradient
+// inputs are grad(lap rho) (gm) and grad(cs^2 rho - p_0) (gr); with the
+// textbook forcing term the collision takes textbook_pairs below.
+template <typename T>
+__device__ __forceinline__ void textbook_pairs(T (&g)[9], T rs, T rho, T ux, T uy, T Fx,
+                                               T Fy, const CollideConsts<T>& q);
+
+template <typename T, int SCH>
 __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
                                         T gry, const CollideConsts<T>& q, T& ux_out,
                                         T& uy_out) {
+  constexpr bool WB = SCH == kSchWB;
   constexpr bool kShifted = sizeof(T) == 4;   // FP32 storage is always shifted
   const T omega = q.omega, kf = q.kf;
   const T rho = rs + q.rho_ref;
@@ -139,6 +154,9 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   if (WB) {
     Fx = -rho * gmx;                                     // Eq. mF
     Fy = -rho * gmy;
+  } else if (SCH == kSchPressure) {
+    Fx = grx + q.kappa * rho * gmx;                      // pressure form
+    Fy = gry + q.kappa * rho * gmy;
   } else {
     Fx = T(1.0 / 3.0) * grx - rho * gmx;                 // potential form
     Fy = T(1.0 / 3.0) * gry - rho * gmy;
@@ -151,6 +169,10 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   const T uy = (jy + T(0.5) * Fy) * inv_rho;
   ux_out = ux;
   uy_out = uy;
+  if (SCH == kSchTextbook) {
+    textbook_pairs<T>(g, rs, rho, ux, uy, Fx, Fy, q);
+    return;
+  }
 
   T Gx = Fx, Gy = Fy;
   if (WB) {
@@ -224,6 +246,46 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   }
 }
 
+// BGK update with the textbook forcing term F_i = (c_i - u).F f_i^eq /
+// (cs^2 rho) = 3 w_i (1 + P_i)(c_i.F - u.F), standard equilibrium
+// f_i^eq - s_i = w_i (rs + rho P_i).  For a pair (i, opposite) with
+// e = 1 + 9/2 (c.u)^2 - 3/2 u.u (the even part of 1 + P_i) the even and odd
+// parts of omega (f^eq - s) + kforce F are
+//   E = omega w (rs + rho (e - 1)) + kforce 3w (3 (c.u)(c.F) - e u.F),
+//   O = omega w rho 3 c.u + kforce 3w (e c.F - 3 (c.u) u.F).
+template <typename T>
+__device__ __forceinline__ void textbook_pairs(T (&g)[9], T rs, T rho, T ux, T uy, T Fx,
+                                               T Fy, const CollideConsts<T>& q) {
+  constexpr bool kShifted = sizeof(T) == 4;
+  const T omega = q.omega, kf = q.kf, keep = q.keep;
+  const T uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+  const T e0 = T(1) - T(1.5) * uu;
+  auto pair = [&](T w, T cu, T cF, T& E, T& O) {
+    const T e = e0 + T(4.5) * cu * cu;
+    E = omega * w * (rs + rho * (e - T(1))) + kf * T(3) * w * (T(3) * cu * cF - e * uF);
+    O = omega * w * rho * T(3) * cu + kf * T(3) * w * (e * cF - T(3) * cu * uF);
+  };
+  T E, O;
+  pair(T(1.0 / 9.0), ux, Fx, E, O);
+  g[1] = keep * g[1] + (E + O);
+  g[3] = keep * g[3] + (E - O);
+  pair(T(1.0 / 9.0), uy, Fy, E, O);
+  g[2] = keep * g[2] + (E + O);
+  g[4] = keep * g[4] + (E - O);
+  pair(T(1.0 / 36.0), ux + uy, Fx + Fy, E, O);
+  g[5] = keep * g[5] + (E + O);
+  g[7] = keep * g[7] + (E - O);
+  pair(T(1.0 / 36.0), uy - ux, Fy - Fx, E, O);
+  g[6] = keep * g[6] + (E + O);
+  g[8] = keep * g[8] + (E - O);
+  if (kShifted) {
+    g[0] = rs - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+  } else {
+    const T w0 = T(4.0 / 9.0);
+    g[0] = keep * g[0] + (omega * w0 * (rs + rho * (e0 - T(1))) - kf * T(3) * w0 * e0 * uF);
+  }
+}
+
 // Isotropic central gradient from the 3x3 neighbourhood:
 //   grad_x = (E - W)/3 + (NE + SE - NW - SW)/12,
 //   grad_y = (N - S)/3 + (NE + NW - SE - SW)/12,
@@ -273,12 +335,47 @@ __device__ __forceinline__ void iso_grad_x2(float2 e, float2 w, float2 n, float2
   gy = fma2(splat(1.0f / 3.0f), sub2(n, s), mul2(splat(1.0f / 12.0f), sub2(d1, d2)));
 }
 
-// collide<float, WB> on a pair of nodes (FP32-shifted storage): the same
+// textbook_pairs<float> on a pair of nodes
+__device__ __forceinline__ void textbook_pairs_x2(float2 (&g)[9], float2 rs, float2 rho,
+                                                  float2 ux, float2 uy, float2 Fx, float2 Fy,
+                                                  const CollideConsts<float>& q) {
+  const float2 omega = splat(q.omega), kf3 = mul2(splat(q.kf), splat(3.0f)), keep = splat(q.keep);
+  const float2 uu = fma2(ux, ux, mul2(uy, uy)), uF = fma2(ux, Fx, mul2(uy, Fy));
+  const float2 e0 = fma2(splat(-1.5f), uu, splat(1.0f));
+  const float2 orho = mul2(omega, rho);
+  auto pair = [&](float w, float2 cu, float2 cF, float2& E, float2& O) {
+    const float2 e = fma2(mul2(splat(4.5f), cu), cu, e0);
+    const float2 em1 = sub2(e, splat(1.0f));
+    const float2 fe = mul2(splat(w), fma2(rho, em1, rs));
+    const float2 fo = mul2(splat(3.0f * w), mul2(orho, cu));
+    const float2 t3 = mul2(splat(3.0f), cu);
+    E = fma2(omega, fe, mul2(mul2(kf3, splat(w)), sub2(mul2(t3, cF), mul2(e, uF))));
+    O = fma2(mul2(kf3, splat(w)), sub2(mul2(e, cF), mul2(t3, uF)), fo);
+  };
+  float2 E, O;
+  pair(1.0f / 9.0f, ux, Fx, E, O);
+  g[1] = fma2(keep, g[1], add2(E, O));
+  g[3] = fma2(keep, g[3], sub2(E, O));
+  pair(1.0f / 9.0f, uy, Fy, E, O);
+  g[2] = fma2(keep, g[2], add2(E, O));
+  g[4] = fma2(keep, g[4], sub2(E, O));
+  pair(1.0f / 36.0f, add2(ux, uy), add2(Fx, Fy), E, O);
+  g[5] = fma2(keep, g[5], add2(E, O));
+  g[7] = fma2(keep, g[7], sub2(E, O));
+  pair(1.0f / 36.0f, sub2(uy, ux), sub2(Fy, Fx), E, O);
+  g[6] = fma2(keep, g[6], add2(E, O));
+  g[8] = fma2(keep, g[8], sub2(E, O));
+  g[0] = sub2(rs, add2(add2(add2(g[1], g[3]), add2(g[2], g[4])),
+                       add2(add2(g[5], g[7]), add2(g[6], g[8]))));
+}
+
+// collide<float, SCH> on a pair of nodes (FP32-shifted storage): the same
 // terms as the scalar version, with the multiply-adds written out.
-template <bool WB>
+template <int SCH>
 __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx, float2 gmy,
                                            float2 grx, float2 gry, const CollideConsts<float>& q,
                                            float2& ux_out, float2& uy_out) {
+  constexpr bool WB = SCH == kSchWB;
   const float2 omega = splat(q.omega), kf = splat(q.kf), third = splat(1.0f / 3.0f);
   const float2 rho = add2(rs, splat(q.rho_ref));
   const float2 nrho = sub2(splat(-q.rho_ref), rs);        // -rho
@@ -286,6 +383,10 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   if (WB) {
     Fx = mul2(nrho, gmx);                                 // Eq. mF
     Fy = mul2(nrho, gmy);
+  } else if (SCH == kSchPressure) {
+    const float2 krho = mul2(splat(q.kappa), rho);        // pressure form
+    Fx = fma2(krho, gmx, grx);
+    Fy = fma2(krho, gmy, gry);
   } else {
     Fx = fma2(third, grx, mul2(nrho, gmx));               // potential form
     Fy = fma2(third, gry, mul2(nrho, gmy));
@@ -300,6 +401,10 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   const float2 uy = mul2(fma2(half, Fy, jy), inv_rho);
   ux_out = ux;
   uy_out = uy;
+  if (SCH == kSchTextbook) {
+    textbook_pairs_x2(g, rs, rho, ux, uy, Fx, Fy, q);
+    return;
+  }
 
   float2 Gx = Fx, Gy = Fy;
   if (WB) {
@@ -530,7 +635,7 @@ __device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo
 // kernel launch reads data that other CTAs wrote during the same launch (L1
 // is not coherent across SMs).  Requires nx >= 8 and pitch >= nx + 12.
 // Offsets within a plane are 32-bit: pitch * ny < 2^31 (checked by the host).
-template <typename T, bool WB, int MODE, int TX, bool GHOST = false>
+template <typename T, int SCH, int MODE, int TX, bool GHOST = false>
 __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restrict__ dst,
                                            const KParams& p, const MomentsOut& mo, int x0,
                                            int y0, int y1, double* stats_rec,
@@ -571,6 +676,26 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 
   const T two_beta = T(p.two_beta), dl = T(p.dl), dg = T(p.dg), kappa6 = T(p.kappa / 6.0);
   const CollideConsts<T> cc(p);
+  // The second ring holds mu, or lap(rho) with the pressure-form force
+  // (chem_pot with beta = 0 and kappa/6 -> -1/6 gives exactly lap(rho)); the
+  // gradient carried to the collision is grad(rho), or grad(cs^2 rho - p_0).
+  constexpr bool kPress = SCH == kSchPressure;
+  const T ring_tb = kPress ? T(0) : two_beta;
+  const T ring_k6 = kPress ? T(-1.0 / 6.0) : kappa6;
+  const T half_beta = T(0.5 * p.two_beta), rho_ref_t = T(p.rho_ref);
+  // cs^2 rho - p_0 from a stored density v (rho = v + rho_ref, up to a
+  // constant): p_0 = rho mu_0 - psi_0 = beta a b (2 rho (a + b) - a b),
+  // a = rho - rho_l, b = rho - rho_g
+  auto press_a = [&](T v) {
+    const T a = v + dl, b = v + dg, r = v + rho_ref_t;
+    return T(1.0 / 3.0) * v - half_beta * a * b * (T(2) * r * (a + b) - a * b);
+  };
+  // mu at a node from its stored density and its second-ring value
+  auto mu_node = [&](T v, T ringval) {
+    if (!kPress) return ringval;
+    const T a = v + dl, b = v + dg;
+    return two_beta * a * b * (a + b) - cc.kappa * ringval;
+  };
   const int kfirst = y0 - 2, klast = y1 + 1;
 
   // 16-byte chunks this thread copies in every row (fixed per thread): in
@@ -677,9 +802,10 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   // rho and grad rho of the last mu row(s) of the previous iteration
   T prs = T(0), pgx = T(0), pgy = T(0);
   float2 prs2 = make_float2(0.f, 0.f), pgx2 = prs2, pgy2 = prs2;
-  const float2 tb2 = make_float2((float)two_beta, (float)two_beta);
+  const float2 tb2 = make_float2((float)ring_tb, (float)ring_tb);
   const float2 dl2 = make_float2((float)dl, (float)dl), dg2 = make_float2((float)dg, (float)dg);
-  const float2 k62 = make_float2((float)kappa6, (float)kappa6);
+  const float2 k62 = make_float2((float)ring_k6, (float)ring_k6);
+  auto press_a2 = [&](float2 v) { return make_float2((float)press_a(T(v.x)), (float)press_a(T(v.y))); };
   // pair (lo[s], hi[s]) of two buffer rows
   auto V = [](const T* lo, const T* hi, int s) { return make_float2((float)lo[s], (float)hi[s]); };
   bool live = true;
@@ -759,9 +885,15 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
               // all loads before the ring stores, so that they are shared
               const float2 mu = at2(sx);
               frs2 = V(rc, ra, sx);
-              iso_grad_x2(V(rc, ra, sx + 1), V(rc, ra, sx - 1), V(ra, rt, sx), V(rb, rc, sx),
-                          V(ra, rt, sx + 1), V(ra, rt, sx - 1), V(rb, rc, sx + 1),
-                          V(rb, rc, sx - 1), fgx2, fgy2);
+              if (kPress)
+                iso_grad_x2(press_a2(V(rc, ra, sx + 1)), press_a2(V(rc, ra, sx - 1)),
+                            press_a2(V(ra, rt, sx)), press_a2(V(rb, rc, sx)),
+                            press_a2(V(ra, rt, sx + 1)), press_a2(V(ra, rt, sx - 1)),
+                            press_a2(V(rb, rc, sx + 1)), press_a2(V(rb, rc, sx - 1)), fgx2, fgy2);
+              else
+                iso_grad_x2(V(rc, ra, sx + 1), V(rc, ra, sx - 1), V(ra, rt, sx), V(rb, rc, sx),
+                            V(ra, rt, sx + 1), V(ra, rt, sx - 1), V(rb, rc, sx + 1),
+                            V(rb, rc, sx - 1), fgx2, fgy2);
               m0[sx] = mu.x;
               m1[sx] = mu.y;
             }
@@ -783,13 +915,18 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
               T* mrow = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
               auto at = [&](int s) {
                 return chem_pot<T>(rc[s], rc[s + 1], rc[s - 1], rn[s], rsb[s], rn[s + 1],
-                                   rn[s - 1], rsb[s + 1], rsb[s - 1], two_beta, dl, dg, kappa6);
+                                   rn[s - 1], rsb[s + 1], rsb[s - 1], ring_tb, dl, dg, ring_k6);
               };
               if (own) {
                 mrow[sx] = at(sx);
                 frs[j] = rc[sx];
-                iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
-                            rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+                if (kPress)
+                  iso_grad<T>(press_a(rc[sx + 1]), press_a(rc[sx - 1]), press_a(rn[sx]),
+                              press_a(rsb[sx]), press_a(rn[sx + 1]), press_a(rn[sx - 1]),
+                              press_a(rsb[sx + 1]), press_a(rsb[sx - 1]), fgx[j], fgy[j]);
+                else
+                  iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
+                              rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
               }
               if (tx == mu_lo) mrow[3] = at(3);
               if (tx == mu_hi) mrow[w + 4] = at(w + 4);
@@ -822,18 +959,18 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                            V(s0, s1, 6 * SW + sx + 1), V(s0, s1, 7 * SW + sx + 1),
                            V(s0, s1, 8 * SW + sx - 1)};
             float2 ux, uy;
-            collide_x2<WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+            collide_x2<SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
             if (v0) {
               const T gl[9] = {g[0].x, g[1].x, g[2].x, g[3].x, g[4].x,
                                g[5].x, g[6].x, g[7].x, g[8].x};
               emit_node<T, MODE, GHOST>(p, mo, dst, c0, xcol, xm, ghost_r, ghost_l, gl, rs.x,
-                                        STATS ? mB[sx] : T(0), ux.x, uy.x, acc, acc_on);
+                                        STATS ? mu_node(rs.x, mB[sx]) : T(0), ux.x, uy.x, acc, acc_on);
             }
             if (v1) {
               const T gh[9] = {g[0].y, g[1].y, g[2].y, g[3].y, g[4].y,
                                g[5].y, g[6].y, g[7].y, g[8].y};
               emit_node<T, MODE, GHOST>(p, mo, dst, c0 + 1, xcol, xm, ghost_r, ghost_l, gh,
-                                        rs.y, STATS ? mC[sx] : T(0), ux.y, uy.y, acc, acc_on);
+                                        rs.y, STATS ? mu_node(rs.y, mC[sx]) : T(0), ux.y, uy.y, acc, acc_on);
             }
           }
           prs2 = frs2;
@@ -860,9 +997,9 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                         st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
                         st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
               T ux, uy;
-              collide<T, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+              collide<T, SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
               emit_node<T, MODE, GHOST>(p, mo, dst, c, xcol, xm, ghost_r, ghost_l, g, rs,
-                                        STATS ? m_c[sx] : T(0), ux, uy, acc, acc_on);
+                                        STATS ? mu_node(rs, m_c[sx]) : T(0), ux, uy, acc, acc_on);
             }
           }
           prs = frs[R - 1];
@@ -919,7 +1056,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 
 // One CTA per strip segment: blockIdx.x picks the strip, blockIdx.y the run
 // of p.rows rows.  Moments mode writes the per-CTA stats record.
-template <typename T, bool WB, bool MOMENTS, int TX>
+template <typename T, int SCH, bool MOMENTS, int TX>
 __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
@@ -930,7 +1067,7 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   double* rec = (MOMENTS && mo.partials)
                     ? mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec
                     : nullptr;
-  strip_pass<T, WB, MOMENTS ? kModeMoments : kModeStep, TX>(src, dst, p, mo, x0, y0, y1, rec,
+  strip_pass<T, SCH, MOMENTS ? kModeMoments : kModeStep, TX>(src, dst, p, mo, x0, y0, y1, rec,
                                                               smem_raw);
 }
 

@@ -1,0 +1,105 @@
+// Host-side launch helpers of the single-lattice strip kernel, templated on
+// the scheme id.  wblbe.cu instantiates them for the standard and the
+// well-balanced scheme, strip_variants.cu for the two comparison variants of
+// the standard scheme (kept in a translation unit of their own so that the
+// units compile in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace wblbe {
+
+template <typename T>
+inline size_t strip_smem(int tile) {
+  return strip_smem_bytes(tile, Staging<T>::kStages, sizeof(T));
+}
+
+// Allow every instantiation the dynamic shared memory it launches with.
+template <typename T, int SCH, bool MOM, int TX>
+cudaError_t allow_smem_tx() {
+  return cudaFuncSetAttribute(lbm_strip_kernel<T, SCH, MOM, TX>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)strip_smem<T>(TX));
+}
+template <typename T, int SCH, bool MOM>
+cudaError_t allow_smem_mom() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = allow_smem_tx<T, SCH, MOM, 32>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, SCH, MOM, 64>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, SCH, MOM, 128>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_tx<T, SCH, MOM, 256>()) != cudaSuccess) e = r;
+  return e;
+}
+template <int SCH>
+cudaError_t allow_smem_scheme() {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = allow_smem_mom<double, SCH, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<double, SCH, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<float, SCH, true>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<float, SCH, false>()) != cudaSuccess) e = r;
+  return e;
+}
+
+template <typename T, int SCH, bool MOM, int TX>
+cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
+                      cudaStream_t s) {
+  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + kp.rows - 1) / kp.rows);
+  lbm_strip_kernel<T, SCH, MOM, TX><<<grid, TX, strip_smem<T>(TX), s>>>(
+      static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
+  return cudaGetLastError();
+}
+
+template <typename T, int SCH, bool MOM>
+cudaError_t launch_strip(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
+                         int tile, cudaStream_t s) {
+  switch (tile) {
+    case 32: return launch_tx<T, SCH, MOM, 32>(src, dst, kp, mo, s);
+    case 64: return launch_tx<T, SCH, MOM, 64>(src, dst, kp, mo, s);
+    case 128: return launch_tx<T, SCH, MOM, 128>(src, dst, kp, mo, s);
+    case 256: return launch_tx<T, SCH, MOM, 256>(src, dst, kp, mo, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int SCH>
+cudaError_t launch_scheme(bool fp64, bool moments, const void* src, void* dst,
+                          const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s) {
+  if (fp64)
+    return moments ? launch_strip<double, SCH, true>(src, dst, kp, mo, tile, s)
+                   : launch_strip<double, SCH, false>(src, dst, kp, mo, tile, s);
+  return moments ? launch_strip<float, SCH, true>(src, dst, kp, mo, tile, s)
+                 : launch_strip<float, SCH, false>(src, dst, kp, mo, tile, s);
+}
+
+// Resident CTAs per SM of the step kernel at this tile width.
+template <typename T, int SCH, int TX>
+int resident_tx() {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_strip_kernel<T, SCH, false, TX>, TX,
+                                                    strip_smem<T>(TX)) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+template <typename T, int SCH>
+int resident_per_sm(int tile) {
+  switch (tile) {
+    case 32: return resident_tx<T, SCH, 32>();
+    case 64: return resident_tx<T, SCH, 64>();
+    case 128: return resident_tx<T, SCH, 128>();
+    default: return resident_tx<T, SCH, 256>();
+  }
+}
+template <int SCH>
+int resident_scheme(bool fp64, int tile) {
+  return fp64 ? resident_per_sm<double, SCH>(tile) : resident_per_sm<float, SCH>(tile);
+}
+
+// The comparison variants (scheme codes 2 and 3), defined in strip_variants.cu.
+cudaError_t launch_variant(int sch, bool fp64, bool moments, const void* src, void* dst,
+                           const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s);
+int resident_variant(int sch, bool fp64, int tile);
+cudaError_t allow_smem_variants();
+
+}  // namespace wblbe

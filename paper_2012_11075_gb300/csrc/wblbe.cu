@@ -16,6 +16,7 @@
 
 #include "../../include/wblbe.h"
 #include "lbm_kernels.cuh"
+#include "strip_launch.cuh"
 
 using namespace wblbe;
 
@@ -49,7 +50,7 @@ bool params_valid(const wblbe_params* p, char* why, size_t n) {
     snprintf(why, n, "need rho_l > rho_g > 0"); return false;
   }
   if (!std::isfinite(p->rho0)) { snprintf(why, n, "rho0 must be finite"); return false; }
-  if (p->scheme != WBLBE_STANDARD && p->scheme != WBLBE_WELL_BALANCED) {
+  if (p->scheme < WBLBE_STANDARD || p->scheme > WBLBE_STANDARD_TEXTBOOK) {
     snprintf(why, n, "unknown scheme %d", p->scheme); return false;
   }
   if (p->precision != WBLBE_FP64 && p->precision != WBLBE_FP32_SHIFTED) {
@@ -193,78 +194,22 @@ bool launch_valid(const wblbe_launch* l) {
   return l->rows_per_cta >= 1;
 }
 
-template <typename T>
-size_t strip_smem(int tile) {
-  return strip_smem_bytes(tile, Staging<T>::kStages, sizeof(T));
-}
-
-// Allow every instantiation the dynamic shared memory it launches with.
-template <typename T, bool WB, bool MOM, int TX>
-cudaError_t allow_smem_tx() {
-  return cudaFuncSetAttribute(lbm_strip_kernel<T, WB, MOM, TX>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)strip_smem<T>(TX));
-}
-template <typename T, bool WB, bool MOM>
-cudaError_t allow_smem() {
-  cudaError_t e = cudaSuccess, r;
-  if ((r = allow_smem_tx<T, WB, MOM, 32>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_tx<T, WB, MOM, 64>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_tx<T, WB, MOM, 128>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_tx<T, WB, MOM, 256>()) != cudaSuccess) e = r;
-  return e;
-}
-
+// Scheme codes 0 (standard) and 1 (well-balanced) are instantiated here, the
+// comparison variants 2 and 3 in strip_variants.cu.
 cudaError_t allow_smem_all() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = allow_smem<double, true, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<double, true, false>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<double, false, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<double, false, false>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<float, true, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<float, true, false>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<float, false, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem<float, false, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_scheme<kSchStandard>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_scheme<kSchWB>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_variants()) != cudaSuccess) e = r;
   return e;
 }
 
-template <typename T, bool WB, bool MOM, int TX>
-cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
-                      cudaStream_t s) {
-  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + kp.rows - 1) / kp.rows);
-  lbm_strip_kernel<T, WB, MOM, TX><<<grid, TX, strip_smem<T>(TX), s>>>(
-      static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
-  return cudaGetLastError();
-}
-
-template <typename T, bool WB, bool MOM>
-cudaError_t launch_strip(const void* src, void* dst, const KParams& kp,
-                         const MomentsOut& mo, int tile, cudaStream_t s) {
-  switch (tile) {
-    case 32: return launch_tx<T, WB, MOM, 32>(src, dst, kp, mo, s);
-    case 64: return launch_tx<T, WB, MOM, 64>(src, dst, kp, mo, s);
-    case 128: return launch_tx<T, WB, MOM, 128>(src, dst, kp, mo, s);
-    case 256: return launch_tx<T, WB, MOM, 256>(src, dst, kp, mo, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-// Resident CTAs per SM of the step kernel at this tile width.
-template <typename T, bool WB, int TX>
-int resident_tx() {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_strip_kernel<T, WB, false, TX>, TX,
-                                                    strip_smem<T>(TX)) != cudaSuccess)
-    return 1;
-  return n > 0 ? n : 1;
-}
-template <typename T, bool WB>
-int resident_per_sm(int tile) {
-  switch (tile) {
-    case 32: return resident_tx<T, WB, 32>();
-    case 64: return resident_tx<T, WB, 64>();
-    case 128: return resident_tx<T, WB, 128>();
-    default: return resident_tx<T, WB, 256>();
+int resident_for(const wblbe_params& p, int tile) {
+  const bool fp64 = p.precision == WBLBE_FP64;
+  switch (p.scheme) {
+    case WBLBE_STANDARD: return resident_scheme<kSchStandard>(fp64, tile);
+    case WBLBE_WELL_BALANCED: return resident_scheme<kSchWB>(fp64, tile);
+    default: return resident_variant(p.scheme, fp64, tile);
   }
 }
 
@@ -277,12 +222,7 @@ wblbe_launch default_launch(const wblbe_params& p) {
   int nsm = kNumSMs, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess)
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const bool wb = p.scheme == WBLBE_WELL_BALANCED;
-  int per_sm;
-  if (p.precision == WBLBE_FP64)
-    per_sm = wb ? resident_per_sm<double, true>(l.tile_x) : resident_per_sm<double, false>(l.tile_x);
-  else
-    per_sm = wb ? resident_per_sm<float, true>(l.tile_x) : resident_per_sm<float, false>(l.tile_x);
+  const int per_sm = resident_for(p, l.tile_x);
   const long long resident = (long long)per_sm * nsm;
   const long long strips = (p.nx + l.tile_x - 1) / l.tile_x;
   long long segs = resident / strips;
@@ -297,17 +237,15 @@ wblbe_launch default_launch(const wblbe_params& p) {
 cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
                        void* dst, const KParams& kp, const MomentsOut& mo,
                        int tile, cudaStream_t s) {
-  const bool wb = h->p.scheme == WBLBE_WELL_BALANCED;
-  if (h->p.precision == WBLBE_FP64) {
-    if (wb) return moments ? launch_strip<double, true, true>(src, dst, kp, mo, tile, s)
-                           : launch_strip<double, true, false>(src, dst, kp, mo, tile, s);
-    return moments ? launch_strip<double, false, true>(src, dst, kp, mo, tile, s)
-                   : launch_strip<double, false, false>(src, dst, kp, mo, tile, s);
+  const bool fp64 = h->p.precision == WBLBE_FP64;
+  switch (h->p.scheme) {
+    case WBLBE_STANDARD:
+      return launch_scheme<kSchStandard>(fp64, moments, src, dst, kp, mo, tile, s);
+    case WBLBE_WELL_BALANCED:
+      return launch_scheme<kSchWB>(fp64, moments, src, dst, kp, mo, tile, s);
+    default:
+      return launch_variant(h->p.scheme, fp64, moments, src, dst, kp, mo, tile, s);
   }
-  if (wb) return moments ? launch_strip<float, true, true>(src, dst, kp, mo, tile, s)
-                         : launch_strip<float, true, false>(src, dst, kp, mo, tile, s);
-  return moments ? launch_strip<float, false, true>(src, dst, kp, mo, tile, s)
-                 : launch_strip<float, false, false>(src, dst, kp, mo, tile, s);
 }
 
 // One step from buf[from] to buf[1-from] on stream s.

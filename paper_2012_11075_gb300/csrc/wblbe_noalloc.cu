@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kTileX* kTileY)
     const double rs = rho_s[ry][rx];
     double ux, uy;
     const CollideConsts<double> cc(p);
-    collide<double, WB>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+    collide<double, WB ? kSchWB : kSchStandard>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
     const double mu = mu_s[my][mx];
     if (rho_out) rho_out[k] = rs;
     if (ux_out) ux_out[k] = ux;

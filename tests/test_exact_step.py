@@ -34,7 +34,7 @@ from fractions import Fraction as Q
 import numpy as np
 import pytest
 
-from oracle.oracle import (STANDARD, STANDARD_GUO, STANDARD_PRESSURE, WELL_BALANCED, Oracle,
+from oracle.oracle import (STANDARD, STANDARD_TEXTBOOK, STANDARD_PRESSURE, WELL_BALANCED, Oracle,
                            Params)
 
 C = [(0, 0), (1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
@@ -153,10 +153,10 @@ CASES = [
     (3, 5, WELL_BALANCED, 0.0, 2.0),
     (3, 3, STANDARD_PRESSURE, 0.0, 0.75),
     (4, 3, STANDARD_PRESSURE, 0.0, 1.25),
-    (3, 3, STANDARD_GUO, 0.0, 0.75),
-    (3, 5, STANDARD_GUO, 0.0, 0.625),
+    (3, 3, STANDARD_TEXTBOOK, 0.0, 0.75),
+    (3, 5, STANDARD_TEXTBOOK, 0.0, 0.625),
 ]
-VARIANT = {STANDARD_PRESSURE: "pressure", STANDARD_GUO: "textbook"}
+VARIANT = {STANDARD_PRESSURE: "pressure", STANDARD_TEXTBOOK: "textbook"}
 
 
 @pytest.mark.parametrize("nx,ny,scheme,rho0,tau", CASES)
@@ -178,7 +178,7 @@ def test_oracle_matches_exact_rational_steps(nx, ny, scheme, rho0, tau):
     args = (Q(tau), Q(kappa), Q(beta), Q(rl), Q(rg), Q(rho0), wb, VARIANT.get(scheme))
     # the textbook term divides by rho each step, which makes the exact
     # denominators grow fast: two steps there (u != 0 from the first on)
-    for step in range(2 if scheme == STANDARD_GUO else 3):
+    for step in range(2 if scheme == STANDARD_TEXTBOOK else 3):
         fq = exact_step(fq, *args)
         orc.step(f, 1)
         fe = _as_float(fq)

@@ -452,8 +452,8 @@ def test_textbook_forcing_moments():
     sum c_i F_i = F, and sum c_a c_b F_i = u_a F_b + F_a u_b
     - u_a u_b (u.F)/cs^2 (from the D2Q9 moments of f^eq); it matches the
     second moment of Eq. Fi up to that O(u^3) term."""
-    from oracle.oracle import CX, CY, STANDARD_GUO
-    o = Oracle(_params(scheme=STANDARD_GUO))
+    from oracle.oracle import CX, CY, STANDARD_TEXTBOOK
+    o = Oracle(_params(scheme=STANDARD_TEXTBOOK))
     os_ = Oracle(_params(scheme=STANDARD))
     rng = np.random.default_rng(11)
     cx, cy = np.array(CX, float), np.array(CY, float)
