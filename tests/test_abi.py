@@ -71,3 +71,38 @@ def test_null_handle_calls_return_einval():
     assert lib.wblbe_init_rho(None, None, 0) == wblbe.EINVAL
     assert lib.wblbe_moments(None, None, None, None, None, 0, None) == wblbe.EINVAL
     assert lib.wblbe_step_count(None) == -1
+
+
+def test_largest_lattice_and_plane_offset_limit():
+    """Plane offsets are 32-bit: a lattice whose padded plane reaches 2^31
+    elements is rejected on the host; 32768 x 32768 (2^30 nodes, 2 x 77 GB in
+    FP64) is accepted, and its workspace covers both population buffers."""
+    lib = wblbe.load_library()
+    ok = _params(nx=32768, ny=32768).c()
+    b = lib.wblbe_workspace_bytes(ctypes.byref(ok))
+    assert b >= 2 * 9 * 32768 * 32768 * 8
+    for nx, ny in [(65536, 32768), (46340, 46341)]:
+        p = _params(nx=nx, ny=ny).c()
+        assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0, (nx, ny)
+
+
+@pytest.mark.parametrize("shape", [(0, 0), (0, 5), (5, 0)])
+def test_empty_lattices_rejected(shape):
+    lib = wblbe.load_library()
+    p = _params(nx=shape[0], ny=shape[1]).c()
+    assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0
+
+
+@pytest.mark.parametrize("scheme", [wblbe.STANDARD_PRESSURE, wblbe.STANDARD_TEXTBOOK])
+def test_variant_schemes_single_lattice_only(scheme):
+    """The Sec. II comparison variants are valid for a single lattice and
+    refused by the batch API (before any device work)."""
+    lib = wblbe.load_library()
+    p = _params(scheme=scheme).c()
+    assert lib.wblbe_workspace_bytes(ctypes.byref(p)) > 0
+    cfg = wblbe.CBatchConfig(128, 32, 1)
+    h = ctypes.c_void_p()
+    st = lib.wblbe_batch_create(scheme, wblbe.FP64, 4, 64, 4096, ctypes.c_void_p(256), 1 << 30,
+                                None, ctypes.byref(cfg), ctypes.byref(h))
+    assert st == wblbe.EINVAL and not h.value
+    assert b"single lattices" in lib.wblbe_batch_last_error(None)
