@@ -351,6 +351,38 @@ def run_serving(args, stream, torch, cfg):
             "results": out}
 
 
+def run_schemes(args, stream, torch):
+    """Cost of the four schemes on the same 4096^2 droplet field (density
+    ratio 5, where the standard scheme is stable too): Sec. III says the
+    well-balanced LBE has the algorithmic structure of the standard one, so
+    they should cost the same.  Step-kernel time by CUDA events."""
+    from paper_2012_11075_gb300 import wblbe
+    from paper_2012_11075_gb300 import workloads as wl
+    pr = wl.large_domain(n=args.lattice, count=64, ratio=5.0, width=5.0, kappa=0.01, tau=0.7)
+    names = {wblbe.STANDARD: "standard", wblbe.WELL_BALANCED: "well_balanced",
+             wblbe.STANDARD_PRESSURE: "standard_pressure_form",
+             wblbe.STANDARD_TEXTBOOK: "standard_textbook_forcing"}
+    out = {"workload": f"large_domain_{pr.nx}x{pr.ny}_64droplets_ratio5", "results": {}}
+    for prec_name, prec, S in (("f32", wblbe.FP32_SHIFTED, 100), ("f64", wblbe.FP64, 20)):
+        for sch, name in names.items():
+            params = wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g,
+                                  scheme=sch, precision=prec)
+            solver = wblbe.Solver(params, stream=stream)
+            solver.init_rho(pr.rho)
+            total, kern, _ = time_device(solver, S, 2, 1, stream, torch)
+            st = solver.stats()
+            kern_avg = kern / (2 * S)
+            out["results"][f"{prec_name}/{name}"] = {
+                "mlups": pr.nx * pr.ny / kern_avg / 1e6, "kernel_us": kern_avg * 1e6,
+                "hbm_frac": BYTES_PER_LU[prec_name] * pr.nx * pr.ny / kern_avg / 1e9 /
+                (measured_peaks().get("hbm_gbs") or 6800.0),
+                "nonfinite": bool(st["nonfinite"])}
+            solver.close()
+            del solver
+            torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2012_11075_gb300 import wblbe
@@ -362,6 +394,10 @@ def run_ours(args, world, rank, local):
     peak_note = "of measured" if hbm_peak else "of fallback"
     hbm_peak = hbm_peak or 6800.0
     stream = torch.cuda.Stream(device=dev)
+    if args.only == "schemes":
+        if rank == 0:
+            print(json.dumps({"schemes": run_schemes(args, stream, torch)}), flush=True)
+        return 0
     if args.only == "batched":
         # the batched leg alone (a partial run, not the benchmark line)
         if rank == 0:
@@ -456,6 +492,8 @@ def run_ours(args, world, rank, local):
                    "f64_umax": r64["umax"], "f64_mass_drift_rel": r64["mass_drift"],
                    "nonfinite": bool(r32["nonfinite"] or r64["nonfinite"])},
     }
+    if not args.no_schemes:
+        line["schemes"] = run_schemes(args, stream, torch)
     if not args.no_batched:
         line["batched"] = run_batched(args, stream, torch)
         if not args.no_serving:
@@ -475,9 +513,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", type=int, default=4096,
                     help="lattice side (4096 is the benchmark; smaller sides are for profiling)")
-    ap.add_argument("--only", choices=["both", "f32", "f64", "batched"], default="both")
+    ap.add_argument("--only", choices=["both", "f32", "f64", "batched", "schemes"],
+                    default="both")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
