@@ -16,7 +16,7 @@ import time
 from pathlib import Path
 
 DEFAULT_CANDIDATES = [(tx, rows, k) for tx in (64, 128, 256) for rows in (16, 32, 64)
-                      for k in (1, 4, 8)]
+                      for k in (1, 4, 8, 16, 32, 64)]
 
 
 def cache_path() -> Path:
