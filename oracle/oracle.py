@@ -35,6 +35,7 @@ WELL_BALANCED = 1
 # variants of the standard LBE compared in Sec. II
 STANDARD_PRESSURE = 2      # pressure-form interaction force
 STANDARD_TEXTBOOK = 3           # forcing term of Guo's textbook
+STANDARD_E6 = 4            # 6th-order isotropic gradient in the force
 
 # D2Q9 velocity set and weights as the paper states them (Sec. II), kept here
 # for tests that need to name a direction.
@@ -87,6 +88,7 @@ def _load(openmp: bool = False):
             fn.restype = ctypes.c_double
         lib.orc_laplacian.argtypes = [pp, dp, dp]
         lib.orc_gradient.argtypes = [pp, dp, dp, dp]
+        lib.orc_gradient6.argtypes = [pp, dp, dp, dp]
         lib.orc_feq.argtypes = [pp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         lib.orc_forcing.argtypes = [pp] + [ctypes.c_double] * 6 + [dp]
         lib.orc_macro.argtypes = [pp, dp] + [dp] * 8
@@ -159,6 +161,13 @@ class Oracle:
         phi = self._field(phi)
         gx, gy = np.empty_like(phi), np.empty_like(phi)
         self._lib.orc_gradient(ctypes.byref(self._cp), _ptr(phi), _ptr(gx), _ptr(gy))
+        return gx, gy
+
+    def gradient6(self, phi):
+        """The radius-2, 6th-order isotropic gradient of the E6 variant."""
+        phi = self._field(phi)
+        gx, gy = np.empty_like(phi), np.empty_like(phi)
+        self._lib.orc_gradient6(ctypes.byref(self._cp), _ptr(phi), _ptr(gx), _ptr(gy))
         return gx, gy
 
     # -- per-node formulas ---------------------------------------------------------

@@ -51,11 +51,12 @@ static const double WQ[Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
 static const double CS2 = 1.0 / 3.0;
 
 /* Schemes: the standard LBE of Sec. II (potential-form force, Eq. Fi), the
- * well-balanced LBE of Sec. III, and two variants of the standard LBE that
- * Sec. II compares it with: the pressure-form force, and the forcing term of
- * Guo's textbook, F_i = (c_i - u).F f_i^eq / (cs^2 rho). */
+ * well-balanced LBE of Sec. III, and variants of the standard LBE that
+ * Sec. II compares it with: the pressure-form force; the forcing term of
+ * Guo's textbook, F_i = (c_i - u).F f_i^eq / (cs^2 rho); and a higher-order
+ * gradient for the force (ORC_STANDARD_E6, see orc_gradient6). */
 enum { ORC_STANDARD = 0, ORC_WELL_BALANCED = 1, ORC_STANDARD_PRESSURE = 2,
-       ORC_STANDARD_TEXTBOOK = 3 };
+       ORC_STANDARD_TEXTBOOK = 3, ORC_STANDARD_E6 = 4 };
 
 /* Problem statement (Sec. IV): lattice, relaxation time, free-energy
  * parameters, the WB constant rho0 (Eq. mFeq) and the scheme. */
@@ -131,6 +132,42 @@ void orc_gradient(const orc_params* p, const double* phi, double* gx,
       }
       gx[node(p, x, y)] = sx / CS2;
       gy[node(p, x, y)] = sy / CS2;
+    }
+}
+
+/* Higher-order isotropic gradient for the force of ORC_STANDARD_E6.  Sec. II
+ * notes that higher-order discretisations of F reduce the spurious velocity
+ * but cannot balance the forces; it names no stencil (reading: the
+ * radius-2 gradient whose weights make the lattice moments isotropic up to
+ * sixth order).  grad(phi) = sum_e W(|e|^2) e phi(x+e) over the shells
+ * |e|^2 = 1 (4 vectors), 2 (4) and 4 (4: (+-2,0), (0,+-2)); the weights solve
+ *   sum W e_x^2 = 1                 (exact on linear functions),
+ *   sum W e_x^4 = 3 sum W e_x^2 e_y^2  (4th-order moments isotropic),
+ *   sum W e_x^6 = 5 sum W e_x^4 e_y^2  (6th-order moments isotropic),
+ * i.e. 2W1 + 4W2 + 8W4 = 1, 2W1 - 8W2 + 32W4 = 0, 2W1 - 16W2 + 128W4 = 0:
+ * W1 = 4/15, W2 = 1/10, W4 = 1/120.  (The 9-point gradient above is the
+ * 4th-order case: W1 = 1/3, W2 = 1/12.) */
+static const double W6_1 = 4.0 / 15.0, W6_2 = 1.0 / 10.0, W6_4 = 1.0 / 120.0;
+
+void orc_gradient6(const orc_params* p, const double* phi, double* gx, double* gy) {
+  static const int EX[12] = {1, 0, -1, 0, 1, -1, -1, 1, 2, 0, -2, 0};
+  static const int EY[12] = {0, 1, 0, -1, 1, 1, -1, -1, 0, 2, 0, -2};
+#pragma omp parallel for
+  for (int y = 0; y < p->ny; ++y)
+    for (int x = 0; x < p->nx; ++x) {
+      double sx = 0.0, sy = 0.0;
+      for (int a = 0; a < 12; ++a) {
+        double w = a < 4 ? W6_1 : (a < 8 ? W6_2 : W6_4);
+        /* offsets up to 2: wrap twice */
+        int xx = x + EX[a], yy = y + EY[a];
+        xx = (xx % p->nx + p->nx) % p->nx;
+        yy = (yy % p->ny + p->ny) % p->ny;
+        double v = phi[(size_t)yy * (size_t)p->nx + (size_t)xx];
+        sx += w * EX[a] * v;
+        sy += w * EY[a] * v;
+      }
+      gx[node(p, x, y)] = sx;
+      gy[node(p, x, y)] = sy;
     }
 }
 
@@ -260,8 +297,13 @@ void orc_macro(const orc_params* p, const double* f, double* rho_out,
   orc_laplacian(p, rho, lap);
 #pragma omp parallel for
   for (size_t k = 0; k < n; ++k) mu[k] = orc_mu0(p, rho[k]) - p->kappa * lap[k];
-  orc_gradient(p, mu, gmx, gmy);
-  orc_gradient(p, rho, grx, gry);
+  if (p->scheme == ORC_STANDARD_E6) {
+    orc_gradient6(p, mu, gmx, gmy);
+    orc_gradient6(p, rho, grx, gry);
+  } else {
+    orc_gradient(p, mu, gmx, gmy);
+    orc_gradient(p, rho, grx, gry);
+  }
   /* pressure form: gmx/gmy become grad(lap rho), and gAx/gAy the gradient of
    * A = cs^2 rho - p_0(rho) */
   double* gAx = NULL;
