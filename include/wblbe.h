@@ -67,10 +67,14 @@ typedef enum {
  *     prints "- kappa grad(lap rho)", which would not equal the potential
  *     form it is said to equal);
  *   WBLBE_STANDARD_TEXTBOOK: potential-form force with the forcing term of
- *     Guo's textbook quoted in Sec. II, F_i = (c_i - u).F f_i^eq/(cs^2 rho).
- * Both use the standard equilibrium Eq. feq (and its FP32 shift). */
+ *     Guo's textbook quoted in Sec. II, F_i = (c_i - u).F f_i^eq/(cs^2 rho);
+ *   WBLBE_STANDARD_E6 (FP64 only): potential-form force whose gradients use
+ *     the radius-2 stencil with moments isotropic to sixth order (weights
+ *     4/15, 1/10, 1/120 on |e|^2 = 1, 2, 4) - Sec. II's "higher-order
+ *     discretisation of F", for which the paper names no stencil.
+ * All use the standard equilibrium Eq. feq (and its FP32 shift). */
 enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1, WBLBE_STANDARD_PRESSURE = 2,
-       WBLBE_STANDARD_TEXTBOOK = 3 };
+       WBLBE_STANDARD_TEXTBOOK = 3, WBLBE_STANDARD_E6 = 4 };
 
 /* Storage/arithmetic precision.
  * WBLBE_FP64: populations stored and updated in float64.
@@ -93,7 +97,7 @@ typedef struct {
   double tau, kappa, beta, rho_l, rho_g;
   double rho0;
   double rho_ref;
-  int32_t scheme;     /* WBLBE_STANDARD .. WBLBE_STANDARD_TEXTBOOK */
+  int32_t scheme;     /* WBLBE_STANDARD .. WBLBE_STANDARD_E6    */
   int32_t precision;  /* WBLBE_FP64 | WBLBE_FP32_SHIFTED        */
 } wblbe_params;
 

@@ -101,5 +101,11 @@ cudaError_t launch_variant(int sch, bool fp64, bool moments, const void* src, vo
                            const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s);
 int resident_variant(int sch, bool fp64, int tile);
 cudaError_t allow_smem_variants();
+// Scheme code 4 (FP64 tile kernel, 32 x 16 nodes per CTA): launch, and the
+// number of per-CTA statistics records its moments pass writes.
+constexpr int kSchE6 = 4;
+cudaError_t launch_e6(bool moments, const void* src, void* dst, const KParams& kp,
+                      const MomentsOut& mo, cudaStream_t s);
+int e6_partials(int nx, int ny);
 
 }  // namespace wblbe

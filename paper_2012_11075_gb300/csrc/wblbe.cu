@@ -50,8 +50,11 @@ bool params_valid(const wblbe_params* p, char* why, size_t n) {
     snprintf(why, n, "need rho_l > rho_g > 0"); return false;
   }
   if (!std::isfinite(p->rho0)) { snprintf(why, n, "rho0 must be finite"); return false; }
-  if (p->scheme < WBLBE_STANDARD || p->scheme > WBLBE_STANDARD_TEXTBOOK) {
+  if (p->scheme < WBLBE_STANDARD || p->scheme > WBLBE_STANDARD_E6) {
     snprintf(why, n, "unknown scheme %d", p->scheme); return false;
+  }
+  if (p->scheme == WBLBE_STANDARD_E6 && p->precision != WBLBE_FP64) {
+    snprintf(why, n, "the E6 comparison scheme runs in FP64 only"); return false;
   }
   if (p->precision != WBLBE_FP64 && p->precision != WBLBE_FP32_SHIFTED) {
     snprintf(why, n, "unknown precision %d", p->precision); return false;
@@ -209,6 +212,7 @@ int resident_for(const wblbe_params& p, int tile) {
   switch (p.scheme) {
     case WBLBE_STANDARD: return resident_scheme<kSchStandard>(fp64, tile);
     case WBLBE_WELL_BALANCED: return resident_scheme<kSchWB>(fp64, tile);
+    case WBLBE_STANDARD_E6: return 1;      // fixed tiles; the launch shape is not used
     default: return resident_variant(p.scheme, fp64, tile);
   }
 }
@@ -243,6 +247,8 @@ cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
       return launch_scheme<kSchStandard>(fp64, moments, src, dst, kp, mo, tile, s);
     case WBLBE_WELL_BALANCED:
       return launch_scheme<kSchWB>(fp64, moments, src, dst, kp, mo, tile, s);
+    case WBLBE_STANDARD_E6:
+      return launch_e6(moments, src, dst, kp, mo, s);
     default:
       return launch_variant(h->p.scheme, fp64, moments, src, dst, kp, mo, tile, s);
   }
@@ -290,7 +296,9 @@ wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,
   KParams kp = make_kparams(h, kMomentsRows);
   MomentsOut mo{rho, ux, uy, mu, h->partials};
   CU(h, launch_any(h, true, h->buf[h->cur], nullptr, kp, mo, tile, h->stream));
-  const int n = ((h->p.nx + tile - 1) / tile) * ((h->p.ny + kMomentsRows - 1) / kMomentsRows);
+  const int n = h->p.scheme == WBLBE_STANDARD_E6
+                    ? e6_partials(h->p.nx, h->p.ny)
+                    : ((h->p.nx + tile - 1) / tile) * ((h->p.ny + kMomentsRows - 1) / kMomentsRows);
   stats_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, n, h->stats_dev);
   CU(h, cudaGetLastError());
   h->launches += 2;

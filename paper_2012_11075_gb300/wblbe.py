@@ -18,8 +18,9 @@ from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ENOTCONVERGED = range(7)
 STANDARD, WELL_BALANCED = 0, 1
-# variants of the standard scheme compared in Sec. II (single lattices only)
-STANDARD_PRESSURE, STANDARD_TEXTBOOK = 2, 3
+# variants of the standard scheme compared in Sec. II (single lattices only;
+# STANDARD_E6 in FP64 only)
+STANDARD_PRESSURE, STANDARD_TEXTBOOK, STANDARD_E6 = 2, 3, 4
 FP64, FP32_SHIFTED = 0, 1
 
 _STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE",

@@ -93,7 +93,8 @@ def test_empty_lattices_rejected(shape):
     assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0
 
 
-@pytest.mark.parametrize("scheme", [wblbe.STANDARD_PRESSURE, wblbe.STANDARD_TEXTBOOK])
+@pytest.mark.parametrize("scheme", [wblbe.STANDARD_PRESSURE, wblbe.STANDARD_TEXTBOOK,
+                                    wblbe.STANDARD_E6])
 def test_variant_schemes_single_lattice_only(scheme):
     """The Sec. II comparison variants are valid for a single lattice and
     refused by the batch API (before any device work)."""
@@ -106,3 +107,9 @@ def test_variant_schemes_single_lattice_only(scheme):
                                 None, ctypes.byref(cfg), ctypes.byref(h))
     assert st == wblbe.EINVAL and not h.value
     assert b"single lattices" in lib.wblbe_batch_last_error(None)
+
+
+def test_e6_scheme_is_fp64_only():
+    lib = wblbe.load_library()
+    p = _params(scheme=wblbe.STANDARD_E6, precision=wblbe.FP32_SHIFTED).c()
+    assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0

@@ -1,11 +1,12 @@
-"""GPU parity of the two comparison variants of the standard LBE (Sec. II):
-the pressure-form interaction force and the textbook forcing term, through
-the C ABI against the FP64 oracle (same tolerances as the main schemes),
-plus the batch API's refusal of them."""
+"""GPU parity of the comparison variants of the standard LBE (Sec. II): the
+pressure-form interaction force, the textbook forcing term and the
+sixth-order isotropic gradient in the force (FP64 only), through the C ABI
+against the FP64 oracle (same tolerances as the main schemes), plus the
+batch API's refusal of them."""
 import numpy as np
 import pytest
 
-from oracle.oracle import STANDARD_PRESSURE, STANDARD_TEXTBOOK
+from oracle.oracle import STANDARD_E6, STANDARD_PRESSURE, STANDARD_TEXTBOOK
 from paper_2012_11075_gb300 import wblbe
 from paper_2012_11075_gb300 import workloads as wl
 from tests.gpu_helpers import need_gpu, pop_error, run_gpu, run_oracle
@@ -13,6 +14,7 @@ from tests.test_gpu_parity import FP32_POP_TOL, FP32_RHO_TOL, FP32_U_TOL, _check
 
 pytestmark = pytest.mark.gpu
 VARIANTS = [STANDARD_PRESSURE, STANDARD_TEXTBOOK]
+FP64_VARIANTS = VARIANTS + [STANDARD_E6]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -22,23 +24,23 @@ def _gpu():
 
 
 def test_codes_match_the_c_abi():
-    assert (wblbe.STANDARD_PRESSURE, wblbe.STANDARD_TEXTBOOK) == (STANDARD_PRESSURE,
-                                                                  STANDARD_TEXTBOOK)
+    assert (wblbe.STANDARD_PRESSURE, wblbe.STANDARD_TEXTBOOK, wblbe.STANDARD_E6) == (
+        STANDARD_PRESSURE, STANDARD_TEXTBOOK, STANDARD_E6)
 
 
-@pytest.mark.parametrize("scheme", VARIANTS)
+@pytest.mark.parametrize("scheme", FP64_VARIANTS)
 def test_fp64_paper_flat_interface(scheme):
     """The 21 x 101 noisy slab of Sec. IV.A (rho_v = 0.2, tau = 0.85)."""
     _check_fp64(wl.paper_flat(), scheme, 1000)
 
 
-@pytest.mark.parametrize("scheme", VARIANTS)
+@pytest.mark.parametrize("scheme", FP64_VARIANTS)
 def test_fp64_paper_droplet(scheme):
     _check_fp64(wl.paper_droplet(), scheme, 1000)
 
 
-@pytest.mark.parametrize("shape", [(3, 3), (1, 17), (17, 1), (67, 129), (257, 33)])
-@pytest.mark.parametrize("scheme", VARIANTS)
+@pytest.mark.parametrize("shape", [(3, 3), (1, 17), (17, 1), (5, 2), (67, 129), (257, 33)])
+@pytest.mark.parametrize("scheme", FP64_VARIANTS)
 def test_fp64_ragged_and_tiny_lattices(shape, scheme):
     nx, ny = shape
     rng = np.random.default_rng(nx * 1000 + ny)
@@ -71,6 +73,6 @@ def test_fp32_shifted_against_oracle(scheme):
 
 
 def test_batch_refuses_the_variants():
-    for scheme in VARIANTS:
+    for scheme in FP64_VARIANTS:
         with pytest.raises(Exception):
             wblbe.Batch(scheme=scheme, max_cases=1, arena_bytes=1 << 20)
