@@ -113,3 +113,16 @@ def test_e6_scheme_is_fp64_only():
     lib = wblbe.load_library()
     p = _params(scheme=wblbe.STANDARD_E6, precision=wblbe.FP32_SHIFTED).c()
     assert lib.wblbe_workspace_bytes(ctypes.byref(p)) == 0
+
+
+def test_workspace_too_small_is_enomem():
+    """The library borrows its workspace: one below wblbe_workspace_bytes is
+    refused with ENOMEM before any device work."""
+    lib = wblbe.load_library()
+    p = _params().c()
+    need = lib.wblbe_workspace_bytes(ctypes.byref(p))
+    h = ctypes.c_void_p()
+    st = lib.wblbe_create(ctypes.byref(p), ctypes.c_void_p(256), need - 256, None,
+                          ctypes.byref(h))
+    assert st == wblbe.ENOMEM and not h.value
+    assert b"needs" in lib.wblbe_last_error(None)

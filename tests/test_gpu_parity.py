@@ -330,3 +330,30 @@ def test_laplace_jump_matches_surface_tension(radius, tol):
     assert abs(dp * radius / sigma - 1.0) < tol
     # both bulk densities sit above saturation (Sec. IV.B), by about W Delta/(24 R)
     assert rin > pr.rho_l and rout > pr.rho_g
+
+
+@pytest.mark.parametrize("precision", [wblbe.FP64, wblbe.FP32_SHIFTED])
+def test_checkpoint_resume_is_exact(precision):
+    """A state saved with get_populations after 50 steps and loaded into a
+    fresh handle with set_populations continues like the run that never
+    stopped: bit for bit in FP64; in FP32-shifted storage the float64 round
+    trip f = g + s, g = f - s can move a stored deviation by one float
+    rounding, which stays at that level."""
+    pr = wl.droplet(n=96, radius=24.0, tau=0.9)
+    from tests.gpu_helpers import gpu_params
+    a = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    a.init_rho(pr.rho)
+    a.step(50)
+    saved = a.get_populations()
+    a.step(70)
+    ref = a.get_populations()
+    a.close()
+    b = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    b.set_populations(saved)
+    b.step(70)
+    got = b.get_populations()
+    b.close()
+    if precision == wblbe.FP64:
+        assert np.array_equal(got, ref)
+    else:
+        assert np.max(np.abs(got - ref)) < 1e-6
