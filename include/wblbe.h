@@ -329,6 +329,16 @@ wblbe_status wblbe_moments_noalloc(const wblbe_params* params, const double* f,
                                    void* cuda_stream);
 const char* wblbe_noalloc_last_error(void);
 
+/* Debugging aid (no counterpart in the paper).  Compute-sanitizer is not
+ * available where this library is tested, so a build with
+ * -DWBLBE_DEBUG_BOUNDS checks every global access of the step, moments and
+ * batched kernels (and the shared-memory slots they compute at run time)
+ * before making it; an access out of its buffer is skipped and counted.
+ * Returns that count on the current device (reset != 0 clears it),
+ * 0xFFFFFFFF in a library built without the checks, 0xFFFFFFFE if the count
+ * could not be read. */
+unsigned int wblbe_debug_bounds_errors(int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

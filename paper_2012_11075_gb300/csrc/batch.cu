@@ -1104,3 +1104,8 @@ wblbe_status wblbe_batch_destroy(wblbe_batch_handle b) {
 const char* wblbe_batch_last_error(wblbe_batch_handle b) { return b ? b->err : g_batch_error; }
 
 }  // extern "C"
+
+namespace wblbe {
+// bounds-check count of this translation unit's kernels (see lbm_kernels.cuh)
+unsigned int batch_bounds_errors(bool reset) { return read_bounds_errors(reset); }
+}  // namespace wblbe

@@ -65,6 +65,34 @@ constexpr int kStatRec = 6;       // mass, kinetic, umax^2, mu_min, mu_max, nonf
 // forcing term F_i = (c_i - u).F f_i^eq / (cs^2 rho) of Guo's textbook.
 enum SchemeId : int { kSchStandard = 0, kSchWB = 1, kSchPressure = 2, kSchTextbook = 3 };
 
+// Bounds-checked build (-DWBLBE_DEBUG_BOUNDS): every global access of the
+// strip kernels and the shared-memory slots computed at run time are checked
+// before use; a bad access is skipped and counted in g_bounds_errors (no
+// trap), which the host reads with wblbe_debug_bounds_errors.  Without the
+// flag the checks compile to nothing.
+#ifdef WBLBE_DEBUG_BOUNDS
+static __device__ unsigned int g_bounds_errors;
+__device__ __forceinline__ bool in_bounds(long long off, long long n) {
+  if (off >= 0 && off < n) return true;
+  atomicAdd(&g_bounds_errors, 1u);
+  return false;
+}
+// host side, per translation unit: read (and optionally clear) the count
+static unsigned int read_bounds_errors(bool reset) {
+  unsigned int v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_bounds_errors, sizeof(v)) != cudaSuccess) return 0xFFFFFFFEu;
+  if (reset) {
+    const unsigned int z = 0;
+    cudaMemcpyToSymbol(g_bounds_errors, &z, sizeof(z));
+  }
+  return v;
+}
+#define WB_IN(off, n) ::wblbe::in_bounds((long long)(off), (long long)(n))
+#else
+static inline unsigned int read_bounds_errors(bool) { return 0xFFFFFFFFu; }
+#define WB_IN(off, n) true
+#endif
+
 __device__ __forceinline__ int wrap_index(int a, int n) {
   int r = a % n;
   return r < 0 ? r + n : r;
@@ -585,17 +613,19 @@ __device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo
                                           StatsAcc& acc, bool acc_on) {
   constexpr bool MOMENTS = MODE == kModeMoments;
   constexpr bool STATS = MODE != kModeStep;
-  if (!MOMENTS) {
+  if (!MOMENTS && WB_IN(c, p.ny) && WB_IN(xcol, p.pitch)) {
     if (GHOST) {
       // parameters live in shared memory here: one running pointer
       T* o = dst + (unsigned)(c * p.pitch + xcol);
       const long long pl = p.plane;
       const int nx = p.nx;
+      const bool gr = ghost_r && WB_IN(xcol + nx, p.pitch);
+      const bool gl = ghost_l && WB_IN(xcol - nx, p.pitch);
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         *o = gv[i];
-        if (ghost_r) o[nx] = gv[i];
-        if (ghost_l) o[-nx] = gv[i];
+        if (gr) o[nx] = gv[i];
+        if (gl) o[-nx] = gv[i];
         o += pl;
       }
     } else {
@@ -609,7 +639,7 @@ __device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo
     const double rho = (double)rs + p.rho_ref;
     const double mu = (double)muc;
     const double dux = (double)ux, duy = (double)uy;
-    if (MOMENTS) {
+    if (MOMENTS && WB_IN(c, p.ny) && WB_IN(xm, p.nx)) {
       const unsigned kk = (unsigned)(c * p.nx + xm);
       if (mo.rho) mo.rho[kk] = rho;
       if (mo.ux) mo.ux[kk] = dux;
@@ -739,7 +769,9 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
         const int roff = cls == 0 ? row_0 : (cls == 1 ? row_m : row_p);
 #pragma unroll
         for (int m = 0; m < CPT; ++m)
-          if (ch_on[cls][m]) cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
+          if (ch_on[cls][m] && WB_IN(ch_src[cls][m] + roff - src, 9 * p.plane - (E - 1)) &&
+              WB_IN(ch_dst[cls][m], 9 * SW - (E - 1)))
+            cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
       }
     } else {
       const int ncols = w + 2 * kPad;
@@ -748,7 +780,8 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           const int roff = dir_cy(i) == -1 ? row_p : (dir_cy(i) == 0 ? row_0 : row_m);
-          cp_async_elem(st + i * SW + j, src + i * p.plane + roff + col);
+          if (WB_IN(i * p.plane + roff + col, 9 * p.plane) && WB_IN(j, SW))
+            cp_async_elem(st + i * SW + j, src + i * p.plane + roff + col);
         }
       }
     }
@@ -835,15 +868,19 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
             const float2 v = rho2(sx);
             if (halo) {
               const float2 h = rho2(hs);
-              r0[hs] = h.x;
-              r1[hs] = h.y;
+              if (WB_IN(hs, SW)) {
+                r0[hs] = h.x;
+                r1[hs] = h.y;
+              }
             }
             r0[sx] = v.x;
             r1[sx] = v.y;
           } else if (halo) {
             const float2 h = rho2(hs);
-            r0[hs] = h.x;
-            r1[hs] = h.y;
+            if (WB_IN(hs, SW)) {
+              r0[hs] = h.x;
+              r1[hs] = h.y;
+            }
           }
         } else {
 #pragma unroll
@@ -851,7 +888,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
             const T* st = stage + WB_SLOT(j, NST) * 9 * SW;
             T* row = rho_s + WB_SLOT(j, kRing) * SW;
             if (own) row[sx] = staged_rho(st, sx);
-            if (halo) row[hs] = staged_rho(st, hs);
+            if (halo && WB_IN(hs, SW)) row[hs] = staged_rho(st, hs);
           }
         }
         // barrier B: every read of the stage slots about to be refilled (rows
@@ -900,8 +937,10 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
             if (tx == mu_lo || tx == mu_hi) {   // halo mu at slots 3 and w+4
               const int s = tx == mu_lo ? 3 : w + 4;
               const float2 mu = at2(s);
-              m0[s] = mu.x;
-              m1[s] = mu.y;
+              if (WB_IN(s, SW)) {
+                m0[s] = mu.x;
+                m1[s] = mu.y;
+              }
             }
           }
         } else {
@@ -929,7 +968,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                               rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
               }
               if (tx == mu_lo) mrow[3] = at(3);
-              if (tx == mu_hi) mrow[w + 4] = at(w + 4);
+              if (tx == mu_hi && WB_IN(w + 4, SW)) mrow[w + 4] = at(w + 4);
             }
           }
         }

@@ -107,5 +107,8 @@ constexpr int kSchE6 = 4;
 cudaError_t launch_e6(bool moments, const void* src, void* dst, const KParams& kp,
                       const MomentsOut& mo, cudaStream_t s);
 int e6_partials(int nx, int ny);
+// Bounds-check counts of the other translation units (bounds-checked build).
+unsigned int variants_bounds_errors(bool reset);
+unsigned int batch_bounds_errors(bool reset);
 
 }  // namespace wblbe

@@ -166,6 +166,8 @@ int resident_variant(int sch, bool fp64, int tile) {
                              : resident_scheme<kSchTextbook>(fp64, tile);
 }
 
+unsigned int variants_bounds_errors(bool reset) { return read_bounds_errors(reset); }
+
 cudaError_t allow_smem_variants() {
   cudaError_t e = cudaSuccess, r;
   if ((r = allow_smem_scheme<kSchPressure>()) != cudaSuccess) e = r;

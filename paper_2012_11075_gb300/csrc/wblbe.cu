@@ -604,3 +604,15 @@ wblbe_status wblbe_destroy(wblbe_handle h) {
 const char* wblbe_last_error(wblbe_handle h) { return h ? h->err : g_thread_error; }
 
 }  // extern "C"
+
+// Out-of-bounds accesses that a library built with -DWBLBE_DEBUG_BOUNDS has
+// seen (and skipped) on the current device, summed over its kernels;
+// 0xFFFFFFFF if the library was built without the checks.
+extern "C" unsigned int wblbe_debug_bounds_errors(int32_t reset) {
+  const unsigned int a = read_bounds_errors(reset != 0);
+  const unsigned int b = batch_bounds_errors(reset != 0);
+  const unsigned int c = variants_bounds_errors(reset != 0);
+  if (a == 0xFFFFFFFFu || b == 0xFFFFFFFFu || c == 0xFFFFFFFFu) return 0xFFFFFFFFu;
+  if (a == 0xFFFFFFFEu || b == 0xFFFFFFFEu || c == 0xFFFFFFFEu) return 0xFFFFFFFEu;
+  return a + b + c;
+}

@@ -9,7 +9,9 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 from dataclasses import dataclass
+from pathlib import Path
 from typing import Optional
 
 import numpy as np
@@ -122,6 +124,7 @@ _SIGNATURES = {
     "wblbe_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(CParams), _P, _P, _P, _P, _P,
                                              ctypes.POINTER(CStats), _P]),
     "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
+    "wblbe_debug_bounds_errors": (ctypes.c_uint, [ctypes.c_int32]),
 }
 
 _lib = None
@@ -132,7 +135,13 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     be built or loaded: there is no fallback implementation."""
     global _lib
     if _lib is None:
-        path = _build.build() if build else _build.LIB_PATH
+        # WBLBE_LIBRARY selects another build of the library, e.g. the
+        # bounds-checked one (_build.build(debug_bounds=True))
+        override = os.environ.get("WBLBE_LIBRARY")
+        if override:
+            path = Path(override)
+        else:
+            path = _build.build() if build else _build.LIB_PATH
         if not path.exists():
             raise ImportError(f"CUDA library {path} is missing; run __graft_entry__.build()")
         lib = ctypes.CDLL(str(path))
@@ -432,3 +441,9 @@ class Batch:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.wblbe_batch_kernel_launches(self.h))
+
+
+def debug_bounds_errors(reset: bool = False) -> int:
+    """Out-of-bounds accesses seen by a bounds-checked build of the library
+    on the current device (0xFFFFFFFF: the loaded library has no checks)."""
+    return int(load_library().wblbe_debug_bounds_errors(1 if reset else 0))
