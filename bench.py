@@ -317,6 +317,10 @@ def run_batched(args, stream, torch):
             "steps_per_case": args.batch_steps, "config": cfg,
             "tuned_from_cache": tuned.get("cached", False), "tuning_mlups": tuned.get("candidates"),
             "admit_s": t_admit, "solve_s": t_solve, "mlups": node_steps / t_solve / 1e6,
+            # whole solve (launch gaps, host checks and tile halos included)
+            # against the same roofline as the headline: 72 B per update
+            "hbm_frac": node_steps * BYTES_PER_LU["f32"] / t_solve / 1e9
+            / (measured_peaks().get("hbm_gbs") or 6800.0),
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "states": states, "state_names": {"1": "converged", "2": "budget", "3": "unstable"},

@@ -16,8 +16,8 @@
 // ring.  The chemical potential
 // mu = mu_0(rho) - kappa lap(rho) of the row below is computed into a second
 // ring, and the row two below the load front is collided: gradients of mu
-// and rho (isotropic central stencil), the interaction force (Eq. mF or the
-// potential form of Sec. II), the velocity (Eq. rhoU), the equilibrium and
+// and rho (isotropic central stencil), the interaction force (Eq. mF, or a
+// force form of Sec. II), the velocity (Eq. rhoU), the equilibrium and
 // forcing terms (Eq. mFeq/mFi or Eq. feq/Fi) and the BGK update are all
 // evaluated in registers, and the nine results are stored to the other
 // buffer.  Each population is read from DRAM once per step (the halo rows and
