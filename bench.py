@@ -492,7 +492,8 @@ def run_ours(args, world, rank, local):
                                   "peak": fp64_peak_tflops, "unit": "TFLOP/s",
                                   "frac": r64["mlups"] * 1e6 * fp64_flops_per_lu / 1e12 / fp64_peak_tflops},
                  "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
-        "health": {"f32_umax": r32["umax"], "f32_mass_drift_rel": r32["mass_drift"],
+        "health": {"f32_lattice_steps": (args.warmup + r32["K"]) * r32["S"],
+                   "f32_umax": r32["umax"], "f32_mass_drift_rel": r32["mass_drift"],
                    "f64_umax": r64["umax"], "f64_mass_drift_rel": r64["mass_drift"],
                    "nonfinite": bool(r32["nonfinite"] or r64["nonfinite"])},
     }
