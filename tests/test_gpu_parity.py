@@ -107,6 +107,18 @@ def test_fp64_ragged_and_tiny_lattices(shape, scheme):
     _check_fp64(pr, scheme, 100)
 
 
+@pytest.mark.parametrize("kappa,tau", [(0.0, 0.85), (0.0128, 2.5), (0.0, 2.5)])
+@pytest.mark.parametrize("scheme", [STANDARD, WELL_BALANCED])
+def test_fp64_degenerate_parameters(kappa, tau, scheme):
+    """kappa = 0 (no gradient term: mu = mu_0) and tau = 2.5 (omega < 1/2,
+    where the collision takes omega = 1 - keep so that keep + omega = 1
+    exactly), on a ragged random field."""
+    rng = np.random.default_rng(77)
+    rho = 0.6 + 0.3 * rng.uniform(-1, 1, (129, 67))
+    pr = wl.Problem(67, 129, tau, kappa, 0.01, 1.0, 0.2, rho, name="degenerate")
+    _check_fp64(pr, scheme, 200)
+
+
 @pytest.mark.parametrize("rho0", [0.2, 0.55])
 def test_fp64_wb_nonzero_rho0(rho0):
     pr = wl.droplet(n=64, radius=16.0, tau=0.9, rho_g=0.2)
