@@ -187,3 +187,38 @@ def test_serving_results_equal_alone_and_in_the_mix():
         f_mix, steps, state = got[r.rid]
         assert steps == info["steps"] and state == info["state"], r.rid
         assert np.array_equal(f_mix, f), r.rid
+
+
+def test_full_mix_in_bench_configuration_sampled_against_solo():
+    """The benchmark's batched workload at full size (all 512 uneven cases,
+    tile 128 x 32, 64 steps per launch) for two launches: sampled cases
+    equal their single-lattice runs bit for bit (non-finite values too, for a
+    case that became unstable), and every case reports its step count."""
+    specs = wl.batched_case_specs(count=512, seed=4)
+
+    def params(sp):
+        return wblbe.Params(sp["nx"], sp["ny"], sp["tau"], sp["kappa"], sp["beta"],
+                            sp["rho_l"], sp["rho_g"], scheme=WELL_BALANCED,
+                            precision=wblbe.FP32_SHIFTED)
+
+    probe = wblbe.Batch(max_cases=1, arena_bytes=1 << 20)
+    total = sum(probe.case_bytes(params(sp)) for sp in specs)
+    probe.close()
+    b = wblbe.Batch(max_cases=512, max_tiles=1 << 18, max_case_nodes=512 * 512,
+                    arena_bytes=int(total * 1.02) + (1 << 20), tile_x=128, rows_per_tile=32,
+                    steps_per_launch=64)
+    ids = [b.admit(params(sp), wl.case_field(sp), 0.0, 10 ** 9) for sp in specs]
+    assert None not in ids
+    b.advance(2)
+    for k in (0, 97, 203, 301, 444, 511):
+        sp, cid = specs[k], ids[k]
+        info = b.info(cid)
+        assert info["steps"] == 128 or info["state"] == wblbe.CASE_UNSTABLE
+        f_mix = b.get_populations(cid, (sp["ny"], sp["nx"]))
+        s = wblbe.Solver(params(sp))
+        s.init_rho(wl.case_field(sp))
+        s.step(info["steps"])
+        f_solo = s.get_populations()
+        s.close()
+        assert np.array_equal(f_mix, f_solo, equal_nan=True), k
+    b.close()
