@@ -91,7 +91,8 @@ enum { WBLBE_FP64 = 0, WBLBE_FP32_SHIFTED = 1 };
  * height beta (> 0) and saturation densities rho_l > rho_g > 0
  * (Eq. doubleWell); rho0 is the numerical constant of Eq. mFeq (the paper
  * uses 0; only the well-balanced scheme reads it); rho_ref is the FP32 shift
- * density (NaN selects (rho_l + rho_g)/2; ignored in FP64). */
+ * density (NaN selects rho_g, which gives the low-density phase the finest
+ * resolution of the stored deviations; ignored in FP64). */
 typedef struct {
   int32_t nx, ny;
   double tau, kappa, beta, rho_l, rho_g;

