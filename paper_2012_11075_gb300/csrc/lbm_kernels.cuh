@@ -547,8 +547,8 @@ template <> struct Staging<float> {
   static constexpr int kAhead = 2;
   static constexpr int kStages = 2 + kRows + kRows * kAhead;     // 8
   __host__ __device__ static constexpr int min_blocks(int tx) { return 640 / tx > 1 ? 640 / tx : 1; }
-  // kernels that keep per-case parameters in registers (batched)
-  __host__ __device__ static constexpr int min_blocks_batch(int tx) { return 65536 / (tx * 128); }
+  // the batched kernel (case parameters in shared memory) fits the same budget
+  __host__ __device__ static constexpr int min_blocks_batch(int tx) { return min_blocks(tx); }
 };
 template <> struct Staging<double> {
   static constexpr int kRows = 1;
