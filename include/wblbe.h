@@ -136,8 +136,9 @@ wblbe_status wblbe_create(const wblbe_params* params, void* dev_workspace,
                           wblbe_handle* out);
 
 /* Change tau, kappa, beta, rho_l, rho_g, rho0 or the scheme between steps.
- * Changing nx, ny, precision or rho_ref returns EINVAL (the stored state
- * depends on them). */
+ * Changing nx, ny or precision, or anything that moves the storage shift
+ * (rho_ref and the scheme in FP32; rho0 of the well-balanced scheme in both
+ * precisions), returns EINVAL: the stored state depends on them. */
 wblbe_status wblbe_set_params(wblbe_handle h, const wblbe_params* params);
 
 /* Choose the launch shape (see wblbe_launch).  EINVAL on unsupported

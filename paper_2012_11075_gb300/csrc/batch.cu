@@ -399,10 +399,6 @@ KParams case_kparams(const wblbe_batch::Case& c, int rows) {
   k.rho_ref = rr;
   k.dl = rr - p.rho_l;
   k.dg = rr - p.rho_g;
-  const double rho0 = (p.scheme == WBLBE_WELL_BALANCED && p.precision == WBLBE_FP64) ? p.rho0 : 0.0;
-  k.wb_b0c = (1.0 - 4.0 / 9.0) * rho0;
-  k.wb_bax = rho0 / 9.0;
-  k.wb_bdg = rho0 / 36.0;
   return k;
 }
 
@@ -417,9 +413,10 @@ LayoutParams case_layout(const wblbe_batch::Case& c) {
   const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                        1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
   const double rr = batch_rho_ref(c.p);
+  // the rest equilibrium at rho_ref (0 in FP64); it carries the WB rho0
+  // vector in both precisions, so the kernel never sees rho0
   for (int i = 0; i < 9; ++i) {
-    if (c.p.precision == WBLBE_FP64) lp.shift[i] = 0.0;
-    else if (lp.wb) lp.shift[i] = (i == 0) ? rr - (1.0 - w[0]) * c.p.rho0 : w[i] * c.p.rho0;
+    if (lp.wb) lp.shift[i] = (i == 0) ? rr - (1.0 - w[0]) * c.p.rho0 : w[i] * c.p.rho0;
     else lp.shift[i] = w[i] * rr;
   }
   return lp;

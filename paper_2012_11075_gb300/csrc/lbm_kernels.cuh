@@ -43,8 +43,6 @@ struct KParams {
   double two_beta;                // 2 beta
   double dl, dg;                  // rho_ref - rho_l, rho_ref - rho_g
   double rho_ref;                 // 0 in FP64
-  double wb_b0c;                  // WB: (1 - w0) rho0 in FP64 storage, else 0
-  double wb_bax, wb_bdg;          // WB: w_axis rho0, w_diag rho0 (FP64), else 0
 };
 
 // Outputs of the moments mode (any pointer may be null).
@@ -124,18 +122,19 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Collision constants in the arithmetic type, converted once per kernel (a
 // float <- double conversion inside the row loop would run on the FP64 pipe).
-// In FP32-shifted storage the rho0 terms of the well-balanced equilibrium
-// cancel against the shift, so only FP64 carries them.
+// The rho0 terms of the well-balanced equilibrium never reach the kernel: in
+// both precisions the planes store deviations from a shift that contains the
+// node-independent rho0 vector (-(1-w0) rho0, w_i rho0), which the BGK update
+// and streaming carry unchanged.
 // keep = 1 - omega must hold exactly in the arithmetic type: the update
 // keep * g + omega * (...) conserves mass only if keep + omega == 1, and a
 // rounded pair would scale the mass every step.  For omega >= 1/2 (tau <= 2)
 // 1 - omega is exact (Sterbenz); for smaller omega, omega is taken as 1 - keep.
 template <typename T>
 struct CollideConsts {
-  T omega, kf, keep, kf_m3, rho_ref, wb_b0c, om_bax, om_bdg, kappa;
+  T omega, kf, keep, kf_m3, rho_ref, kappa;
   __device__ explicit CollideConsts(const KParams& p)
-      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)),
-        wb_b0c(T(p.wb_b0c)), om_bax(T(p.omega * p.wb_bax)), om_bdg(T(p.omega * p.wb_bdg)) {
+      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)) {
     const T w = T(p.omega);
     if (w >= T(0.5)) {
       omega = w;
@@ -218,13 +217,7 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
     E0 = T(4.0 / 9.0) * (t - ku);
     Cax = T(1.0 / 9.0) * (t + T(0.5) * ku);
     Cdg = T(1.0 / 36.0) * (t + T(2) * ku);
-    if (kShifted) {
-      E0 = E0 + omega * rs;                            // b_0 = rs, b_ax = b_dg = 0
-    } else {
-      E0 = E0 + omega * (rs - q.wb_b0c);
-      Cax = Cax + q.om_bax;
-      Cdg = Cdg + q.om_bdg;
-    }
+    E0 = E0 + omega * rs;                              // b_0 = rs, b_ax = b_dg = 0
   } else {
     const T s = t + omega * rs;                        // b_i = w_i rs
     E0 = T(4.0 / 9.0) * s;

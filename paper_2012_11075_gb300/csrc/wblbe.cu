@@ -163,12 +163,20 @@ KParams make_kparams(const wblbe_ctx* h, int rows) {
   k.rho_ref = rr;
   k.dl = rr - p.rho_l;
   k.dg = rr - p.rho_g;
-  const bool fp64 = p.precision == WBLBE_FP64;
-  const double rho0 = (p.scheme == WBLBE_WELL_BALANCED && fp64) ? p.rho0 : 0.0;
-  k.wb_b0c = (1.0 - 4.0 / 9.0) * rho0;
-  k.wb_bax = rho0 / 9.0;
-  k.wb_bdg = rho0 / 36.0;
   return k;
+}
+
+// The stored shift s_i of a parameter set (see make_layout_params).
+void shift_of(const wblbe_params& p, double s[9]) {
+  const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
+                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+  const double rr = rho_ref_of(p);
+  for (int i = 0; i < 9; ++i) {
+    if (p.scheme == WBLBE_WELL_BALANCED)
+      s[i] = (i == 0) ? rr - (1.0 - w[0]) * p.rho0 : w[i] * p.rho0;
+    else
+      s[i] = w[i] * rr;
+  }
 }
 
 LayoutParams make_layout_params(const wblbe_ctx* h) {
@@ -180,19 +188,9 @@ LayoutParams make_layout_params(const wblbe_ctx* h) {
   lp.plane = h->L.plane;
   lp.wb = p.scheme == WBLBE_WELL_BALANCED;
   lp.rho0 = p.rho0;
-  const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
-                       1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-  if (p.precision == WBLBE_FP64) {
-    for (int i = 0; i < 9; ++i) lp.shift[i] = 0.0;
-  } else {
-    const double rr = rho_ref_of(p);
-    for (int i = 0; i < 9; ++i) {
-      if (lp.wb)
-        lp.shift[i] = (i == 0) ? rr - (1.0 - w[0]) * p.rho0 : w[i] * p.rho0;
-      else
-        lp.shift[i] = w[i] * rr;
-    }
-  }
+  // the rest equilibrium at rho_ref (0 in FP64); it carries the WB rho0
+  // vector in both precisions, so the kernel never sees rho0
+  shift_of(p, lp.shift);
   return lp;
 }
 
@@ -403,11 +401,17 @@ wblbe_status wblbe_set_params(wblbe_handle h, const wblbe_params* params) {
   if (!params_valid(params, why, sizeof(why))) return fail(h, WBLBE_EINVAL, "%s", why);
   if (params->nx != h->p.nx || params->ny != h->p.ny || params->precision != h->p.precision)
     return fail(h, WBLBE_EINVAL, "nx, ny and precision are fixed for a handle");
-  if (params->precision == WBLBE_FP32_SHIFTED &&
-      (rho_ref_of(*params) != rho_ref_of(h->p) ||
-       (params->scheme != h->p.scheme) || (params->rho0 != h->p.rho0 &&
-                                           params->scheme == WBLBE_WELL_BALANCED)))
-    return fail(h, WBLBE_EINVAL, "the FP32 shift (rho_ref, scheme, rho0) is fixed for a handle");
+  {
+    // the stored state is a deviation from the shift: it may not change
+    double s_old[9], s_new[9];
+    shift_of(h->p, s_old);
+    shift_of(*params, s_new);
+    for (int i = 0; i < 9; ++i)
+      if (s_old[i] != s_new[i])
+        return fail(h, WBLBE_EINVAL,
+                    "the storage shift (rho_ref and scheme in FP32, rho0 of the "
+                    "well-balanced scheme) is fixed for a handle");
+  }
   h->p = *params;
   drop_graph(h);
   return WBLBE_OK;

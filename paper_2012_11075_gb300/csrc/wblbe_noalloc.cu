@@ -217,10 +217,6 @@ wblbe_status wblbe_moments_noalloc(const wblbe_params* params, const double* f,
   kp.dl = -params->rho_l;
   kp.dg = -params->rho_g;
   kp.rho_ref = 0.0;
-  const double rho0 = params->scheme == WBLBE_WELL_BALANCED ? params->rho0 : 0.0;
-  kp.wb_b0c = (1.0 - 4.0 / 9.0) * rho0;
-  kp.wb_bax = rho0 / 9.0;
-  kp.wb_bdg = rho0 / 36.0;
 
   dim3 grid((unsigned)gx, (unsigned)gy), block(kTileX, kTileY);
   if (params->scheme == WBLBE_WELL_BALANCED)

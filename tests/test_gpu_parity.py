@@ -287,6 +287,11 @@ def test_invalid_calls_and_unstable_state():
         s.set_params(bad)
     with pytest.raises(wblbe.WblbeError):
         s.set_launch(48, 4)
+    ok = gpu_params(pr, WELL_BALANCED)
+    ok.tau = 0.9
+    s.set_params(ok)                                  # physics may change
+    with pytest.raises(wblbe.WblbeError):             # the storage shift may not
+        s.set_params(gpu_params(pr, WELL_BALANCED, rho0=0.3))
     rho = pr.rho.copy()
     rho[5, 7] = math.nan
     s.init_rho(rho)
