@@ -77,7 +77,10 @@ enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1, WBLBE_STANDARD_PRESSURE = 2,
        WBLBE_STANDARD_TEXTBOOK = 3, WBLBE_STANDARD_E6 = 4 };
 
 /* Storage/arithmetic precision.
- * WBLBE_FP64: populations stored and updated in float64.
+ * WBLBE_FP64: populations stored and updated in float64 (for the
+ *   well-balanced scheme as deviations from the constant rho0 vector
+ *   s_0 = -(1-w_0) rho0, s_i = w_i rho0, the shift below at rho_ref = 0; the
+ *   update carries it unchanged, and get/set_populations use f_i itself).
  * WBLBE_FP32_SHIFTED: populations stored as float32 deviations
  *   g_i = f_i - s_i from the scheme's rest equilibrium s_i at rho_ref
  *   (standard: s_i = w_i rho_ref; well-balanced: s_0 = rho_ref - (1-w_0) rho0,
