@@ -721,6 +721,36 @@ wblbe_status case_moments(wblbe_batch* b, const wblbe_batch::Case& c, double* rh
   return WBLBE_OK;
 }
 
+// Device part of an admission: the initial state f = f^eq(rho, 0) of case
+// slot from the host field rho, its case-table entry and its initial mass.
+wblbe_status admit_device(wblbe_batch* b, int slot, const double* rho) {
+  wblbe_batch::Case& c = b->cases[slot];
+  const wblbe_params& p = c.p;
+  const size_t nodes = (size_t)p.nx * p.ny;
+  BCU(b, cudaMemcpyAsync(b->d_stage, rho, nodes * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  LayoutParams lp = case_layout(c);
+  dim3 grid((p.nx + 2 * kPad + 127) / 128, p.ny);
+  const int wb = p.scheme == WBLBE_WELL_BALANCED;
+  if (b->precision == WBLBE_FP64)
+    batch_init_kernel<double><<<grid, 128, 0, b->stream>>>(
+        b->d_stage, reinterpret_cast<double*>(b->arena + c.off), p.nx, p.ny, c.pitch, c.plane,
+        wb, p.rho0, lp);
+  else
+    batch_init_kernel<float><<<grid, 128, 0, b->stream>>>(
+        b->d_stage, reinterpret_cast<float*>(b->arena + c.off), p.nx, p.ny, c.pitch, c.plane,
+        wb, p.rho0, lp);
+  BCU(b, cudaGetLastError());
+  wblbe_status st = upload_case_entry(b, slot);
+  if (st != WBLBE_OK) return st;
+  st = case_moments(b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (st != WBLBE_OK) return st;
+  double v[kStatRec];
+  BCU(b, cudaMemcpyAsync(v, scratch_stats(b), sizeof(v), cudaMemcpyDeviceToHost, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));
+  c.mass0 = v[0];
+  return WBLBE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -882,31 +912,15 @@ wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
   c.bytes = bytes;
   c.tol = umax_tol;
   c.max_steps = max_steps;
-  b->next_id++;
-  // initial state
-  const size_t nodes = (size_t)params->nx * params->ny;
-  BCU(b, cudaMemcpyAsync(b->d_stage, rho, nodes * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-  LayoutParams lp = case_layout(c);
-  dim3 grid((params->nx + 2 * kPad + 127) / 128, params->ny);
-  const int wb = params->scheme == WBLBE_WELL_BALANCED;
-  if (b->precision == WBLBE_FP64)
-    batch_init_kernel<double><<<grid, 128, 0, b->stream>>>(
-        b->d_stage, reinterpret_cast<double*>(b->arena + c.off), params->nx, params->ny, c.pitch,
-        c.plane, wb, params->rho0, lp);
-  else
-    batch_init_kernel<float><<<grid, 128, 0, b->stream>>>(
-        b->d_stage, reinterpret_cast<float*>(b->arena + c.off), params->nx, params->ny, c.pitch,
-        c.plane, wb, params->rho0, lp);
-  BCU(b, cudaGetLastError());
   b->tiles_dirty = true;                  // the tile table is rebuilt before the next launch
-  wblbe_status st = upload_case_entry(b, slot);
-  if (st != WBLBE_OK) return st;
-  st = case_moments(b, c, nullptr, nullptr, nullptr, nullptr, nullptr);
-  if (st != WBLBE_OK) return st;
-  double v[kStatRec];
-  BCU(b, cudaMemcpyAsync(v, scratch_stats(b), sizeof(v), cudaMemcpyDeviceToHost, b->stream));
-  BCU(b, cudaStreamSynchronize(b->stream));
-  c.mass0 = v[0];
+  const wblbe_status st = admit_device(b, slot, rho);
+  if (st != WBLBE_OK) {
+    // give the slot and its arena range back (the message stays in b->err)
+    free_range(b, c.off, c.bytes);
+    c = wblbe_batch::Case();
+    return st;
+  }
+  b->next_id++;
   *case_id = c.id;
   return WBLBE_OK;
 }

@@ -471,20 +471,23 @@ wblbe_status wblbe_step(wblbe_handle h, int64_t nsteps) {
       CU(h, issue_step(h, 1, h->stream));
       h->cur = 0;
       h->launches += 1;
+      h->steps += 1;
       --left;
     }
     while (left >= kGraphSteps) {
       CU(h, cudaGraphLaunch(h->graph, h->stream));
       h->launches += kGraphSteps;
+      h->steps += kGraphSteps;
       left -= kGraphSteps;
     }
   }
+  // the step count follows what was issued, also when a launch fails midway
   for (; left > 0; --left) {
     CU(h, issue_step(h, h->cur, h->stream));
     h->cur ^= 1;
     h->launches += 1;
+    h->steps += 1;
   }
-  h->steps += nsteps;
   return WBLBE_OK;
 }
 
