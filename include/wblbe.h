@@ -157,7 +157,8 @@ wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho,
 
 /* Advance nsteps >= 0 time steps of Eq. D2Q9 (collision, streaming,
  * periodic boundaries).  Asynchronous on the handle's stream; repeated
- * chunks are replayed from a captured CUDA graph. */
+ * chunks are replayed from a captured CUDA graph.  On ECUDA the step count
+ * (wblbe_step_count) includes the steps issued before the failing launch. */
 wblbe_status wblbe_step(wblbe_handle h, int64_t nsteps);
 
 /* Step until max|u| < umax_tol, testing every check_every steps (> 0), or
@@ -262,7 +263,8 @@ wblbe_status wblbe_batch_set_wait_limit(wblbe_batch_handle b, int64_t spins);
  * initial density rho ([ny][nx] float64, host), the max|u| tolerance that
  * counts as equilibrium and a step budget.  The case starts at rest,
  * f = f^eq(rho, 0).  ENOMEM when no case slot, arena range or tile-table room
- * is free: the caller keeps the request queued and retries after a retire. */
+ * is free: the caller keeps the request queued and retries after a retire.
+ * On any error the case is not admitted: its slot and arena range stay free. */
 wblbe_status wblbe_batch_admit(wblbe_batch_handle b, const wblbe_params* params,
                                const double* rho, double umax_tol,
                                int64_t max_steps, int64_t* case_id);
