@@ -272,6 +272,33 @@ def test_well_balanced_flat_interface_reaches_discrete_equilibrium(rho0):
     assert np.max(np.abs(m["mu"] - mu_bar)) < 1e-13
 
 
+def test_discrete_equilibrium_approaches_tanh_at_second_order():
+    """The Newton solution of the discrete balance (3-point Laplacian) tends
+    to the continuous flat-interface profile of Eq. Tanh as the interface
+    widens: the truncation error of the Laplacian is O((dx/W)^2), so doubling
+    W divides the largest deviation by about 4 (a wrong kappa factor, sign or
+    stencil weight in the solver would leave an O(1) or O(1/W) gap).  Far
+    from the interfaces the densities are the double-well minima up to the
+    exponential tail of tanh, exp(-4 L / W) with L the distance to the
+    nearest interface."""
+    kappa, rl, rg, ny = 0.01, 1.0, 0.1, 512
+    dev = {}
+    for width in (4.0, 8.0, 16.0):
+        beta = eq.beta_for_width(kappa, width, rl, rg)
+        prof = _slab(ny, width=width, rho_l=rl, rho_g=rg, half=ny / 4)
+        r, mu_bar = eq.discrete_flat_equilibrium(prof, kappa, beta, rl, rg)
+        lap = np.roll(r, 1) + np.roll(r, -1) - 2.0 * r
+        assert np.max(np.abs(eq.mu0(r, beta, rl, rg) - kappa * lap - mu_bar)) < 1e-15
+        assert abs(r.sum() - prof.sum()) < 1e-11
+        tail = math.exp(-4.0 * (ny / 4) / width)
+        assert abs(r[ny // 2] - rl) < 1e-12 + 2 * tail      # liquid bulk (d = ny / 2)
+        assert abs(r[0] - rg) < 1e-12 + 2 * tail             # vapour bulk (d = 0)
+        dev[width] = np.max(np.abs(r - prof))
+    assert 1e-3 < dev[4.0] < 1e-2
+    for a, b in ((4.0, 8.0), (8.0, 16.0)):
+        assert 3.6 < dev[a] / dev[b] < 4.6, dev
+
+
 def test_equilibrium_profile_is_fixed_point_of_wb_not_of_standard():
     """Start both schemes from the discrete equilibrium of a wide slab at the
     paper's parameters (rho_v = 0.2, beta = 0.01, kappa = 0.0128, tau = 0.85).
