@@ -1,7 +1,8 @@
 """The constant rho0 of the well-balanced equilibrium on the GPU (Sec. III):
 it leaves the equilibrium state unchanged, and the stability map over
 (rho0, density ratio, tau) runs through the batched kernel.  Host-side table
-formatting is checked on the CPU."""
+formatting, and a slow transverse instability of the WB flat interface at
+tau = 0.8 on the oracle, are checked on the CPU."""
 import numpy as np
 import pytest
 
@@ -92,3 +93,34 @@ def test_rho0_is_an_exact_offset_on_gpu(precision):
     b = np.concatenate([[-(1 - w[0]) * 0.3], w[1:] * 0.3])
     tol = 1e-12 if precision == "fp64" else 2e-6
     assert np.max(np.abs(f3 - f0 - b[:, None, None])) < tol
+
+
+@pytest.mark.parametrize("tau,grows", [(0.8, True), (0.85, False)])
+def test_wb_flat_interface_transverse_mode(tau, grows):
+    """Oracle (CPU, FP64): the WB flat slab 4 x 201 (ratio 10, W = 4) seeded
+    with a density perturbation of 1e-10 that alternates along x.  At
+    tau = 0.8 the x-alternating mode grows exponentially (about x8 per 4000
+    steps), at tau = 0.85 it decays.  Runs that keep exact x-uniformity never
+    seed this mode, which is why the deterministic slab at tau = 0.8 stays
+    finite while any per-step noise (e.g. stochastic rounding) destroys it."""
+    from oracle.oracle import Oracle, Params, WELL_BALANCED
+    from paper_2012_11075_gb300 import workloads as wl
+    pr = wl.flat_interface(nx=4, ny=201, tau=tau)
+    o = Oracle(Params(pr.nx, pr.ny, tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g, 0.0,
+                      WELL_BALANCED))
+    rho = pr.rho + 1e-10 * (-1.0) ** np.arange(4)[None, :] * \
+        np.random.default_rng(7).uniform(-1, 1, (201, 1))
+    f = o.init(rho)
+
+    def amp():
+        r = o.macro(f)["rho"]
+        return np.max(np.abs(r - r.mean(axis=1, keepdims=True)))
+
+    o.step(f, 4000)
+    a0 = amp()
+    o.step(f, 16000)
+    a1 = amp()
+    if grows:
+        assert a1 > 1e3 * a0, (a0, a1)
+    else:
+        assert a1 < a0, (a0, a1)
