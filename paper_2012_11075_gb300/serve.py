@@ -7,7 +7,9 @@ room are free, advances every resident running case together one persistent
 launch at a time, and retires each case as soon as it stops (converged,
 budget reached or unstable), which frees its memory for the next admission.
 Requests that arrive while others are on the device therefore share launches
-with them.  Latency is completion time minus arrival time.
+with them.  Latency is completion time minus arrival time.  A request that
+the batch refuses while it holds no case can never fit (it is larger than
+the whole arena or tile table): it is rejected instead of blocking the queue.
 
 The batch object is injected (``paper_2012_11075_gb300.wblbe.Batch`` on the
 GPU); the loop itself is host logic and is tested on the CPU with a fake.
@@ -20,6 +22,9 @@ import time
 from dataclasses import dataclass, field
 
 import numpy as np
+
+
+REJECTED = -2                   # Request.state of a request that can never fit
 
 
 @dataclass
@@ -40,6 +45,7 @@ class Request:
 @dataclass
 class ServeReport:
     completed: list = field(default_factory=list)
+    rejected: list = field(default_factory=list)
     offered: int = 0
     admitted: int = 0
     backlog: int = 0
@@ -58,6 +64,7 @@ class ServeReport:
             "offered": self.offered,
             "admitted": self.admitted,
             "completed": len(self.completed),
+            "rejected": len(self.rejected),
             "backlog_at_end": self.backlog,
             "running_at_end": self.running_at_end,
             "elapsed_s": self.elapsed,
@@ -97,7 +104,14 @@ class Server:
                 req.rho = req.rho()            # built when it is first offered
             cid = self.batch.admit(req.params, req.rho, req.umax_tol, req.max_steps)
             if cid is None:
-                break                          # full: keep it queued
+                if self.resident:
+                    break                      # full: keep it queued
+                # refused by an empty batch: it will never fit
+                self.queue.popleft()
+                req.state = REJECTED
+                req.finished = self.now()
+                self.report.rejected.append(req)
+                continue
             self.queue.popleft()
             req.case_id = cid
             req.admitted = self.now()

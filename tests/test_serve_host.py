@@ -145,3 +145,27 @@ def test_autotune_picks_fastest_and_caches(tmp_path, monkeypatch):
     again = autotune.tune(b, shapes, "FakeGPU", candidates=cands, launches=2)
     assert again["cached"] and b.cfg == (128, 32, 8)
     assert autotune.size_class(shapes) == autotune.size_class(list(reversed(shapes)))
+
+
+class BoundedBatch(FakeBatch):
+    """Refuses any case whose `need` exceeds `limit`, even when empty."""
+
+    def __init__(self, slots, limit):
+        super().__init__(slots)
+        self.limit = limit
+
+    def admit(self, params, rho, tol, max_steps):
+        if int(rho) > self.limit:
+            return None
+        return super().admit(params, rho, tol, max_steps)
+
+
+def test_request_that_never_fits_is_rejected_not_blocking():
+    b = BoundedBatch(slots=1, limit=10)
+    srv = serve.Server(b, clock=FakeClock())
+    reqs = [_req(0, 0.0, 3), _req(1, 0.0, 50), _req(2, 0.0, 2)]
+    rep = srv.run(reqs, duration=0.0, drain=True)
+    assert sorted(r.rid for r in rep.completed) == [0, 2]
+    assert [r.rid for r in rep.rejected] == [1] and rep.rejected[0].state == serve.REJECTED
+    s = rep.summary()
+    assert s["rejected"] == 1 and s["backlog_at_end"] == 0
