@@ -68,7 +68,8 @@ def tune(batch, shapes, gpu_name: str, candidates=None, launches: int = 3,
     """Pick the fastest configuration for the cases resident in ``batch``
     (their lattice shapes are ``shapes``); the batch is left configured with
     it.  Timing advances the resident cases.  Returns the winning entry
-    (config and measured rate of every candidate)."""
+    (config and measured rate of every candidate).  If the cases stop before
+    any candidate could be timed, the first candidate is kept, uncached."""
     key = cache_key(gpu_name, batch.precision, batch.scheme, shapes)
     if use_cache:
         hit = load_cache().get(key)
@@ -91,6 +92,10 @@ def tune(batch, shapes, gpu_name: str, candidates=None, launches: int = 3,
         if running == 0 or dt <= 0:
             break
         rates[f"{cand[0]}x{cand[1]}x{cand[2]}"] = nodes * cand[2] * launches / dt / 1e6
+    cands = list(candidates or DEFAULT_CANDIDATES)
+    if not rates:
+        batch.set_config(*cands[0])
+        return {"config": list(cands[0]), "mlups": None, "candidates": {}, "cached": False}
     best = max(rates, key=rates.get)
     cfg = tuple(int(v) for v in best.split("x"))
     batch.set_config(*cfg)

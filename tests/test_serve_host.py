@@ -169,3 +169,15 @@ def test_request_that_never_fits_is_rejected_not_blocking():
     assert [r.rid for r in rep.rejected] == [1] and rep.rejected[0].state == serve.REJECTED
     s = rep.summary()
     assert s["rejected"] == 1 and s["backlog_at_end"] == 0
+
+
+def test_autotune_with_cases_that_stop_at_once(tmp_path, monkeypatch):
+    """Every resident case stops during the first warm-up launch: nothing can
+    be timed, the first candidate is kept and nothing is cached."""
+    monkeypatch.setenv("WBLBE_TUNE_CACHE", str(tmp_path / "tune.json"))
+    b = FakeBatch(slots=2)
+    b.admit(None, 1, 0, 0)
+    cands = [(64, 16, 8), (128, 32, 8)]
+    out = autotune.tune(b, [(64, 64)], "FakeGPU", candidates=cands, launches=2)
+    assert out["config"] == [64, 16, 8] and out["mlups"] is None and not out["cached"]
+    assert b.cfg == (64, 16, 8) and not (tmp_path / "tune.json").exists()
