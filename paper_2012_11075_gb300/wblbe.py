@@ -178,6 +178,14 @@ def workspace_bytes(params: Params) -> int:
     return int(load_library().wblbe_workspace_bytes(ctypes.byref(cp)))
 
 
+def _require(cond: bool, what: str):
+    """Argument check that stays active under ``python -O``: the C side reads
+    and writes as many elements as the lattice has, so a wrong shape, dtype
+    or layout must never reach it."""
+    if not cond:
+        raise ValueError(what)
+
+
 def _ptr(x) -> int:
     """Device or host address of a torch tensor or numpy array."""
     if isinstance(x, np.ndarray):
@@ -253,11 +261,12 @@ class Solver:
         pinned or not) or a CUDA tensor (device memory)."""
         if isinstance(rho, np.ndarray):
             rho = np.ascontiguousarray(rho, dtype=np.float64)
-            assert rho.shape == self.shape
+            _require(rho.shape == self.shape, f"rho must have shape {self.shape}")
             self._check(self.lib.wblbe_init_rho(self.h, ctypes.c_void_p(rho.ctypes.data), 0))
         else:
-            assert rho.dtype == self._torch.float64 and rho.is_contiguous()
-            assert tuple(rho.shape) == self.shape
+            _require(rho.dtype == self._torch.float64 and rho.is_contiguous(),
+                     "rho must be a contiguous float64 tensor")
+            _require(tuple(rho.shape) == self.shape, f"rho must have shape {self.shape}")
             self._check(self.lib.wblbe_init_rho(self.h, ctypes.c_void_p(rho.data_ptr()),
                                                 1 if rho.is_cuda else 0))
 
@@ -267,6 +276,16 @@ class Solver:
         outs = [rho, ux, uy, mu]
         given = [o for o in outs if o is not None]
         on_dev = bool(given) and not isinstance(given[0], np.ndarray) and given[0].is_cuda
+        for o in given:
+            if isinstance(o, np.ndarray):
+                ok = o.dtype == np.float64 and o.flags.c_contiguous and o.flags.writeable
+                dev = False
+            else:
+                ok = o.dtype == self._torch.float64 and o.is_contiguous()
+                dev = o.is_cuda
+            _require(ok and tuple(o.shape) == self.shape,
+                     f"outputs must be contiguous writable float64 of shape {self.shape}")
+            _require(dev == on_dev, "outputs must be all on the host or all on the device")
         ptrs = [None if o is None else ctypes.c_void_p(_ptr(o)) for o in outs]
         st = CStats()
         self._check(self.lib.wblbe_moments(self.h, *ptrs, 1 if on_dev else 0, ctypes.byref(st)))
@@ -309,7 +328,7 @@ class Solver:
 
     def set_populations(self, f: np.ndarray):
         f = np.ascontiguousarray(f, dtype=np.float64)
-        assert f.shape == (9,) + self.shape
+        _require(f.shape == (9,) + self.shape, f"f must have shape {(9,) + self.shape}")
         self._check(self.lib.wblbe_set_populations(self.h, ctypes.c_void_p(f.ctypes.data), 0))
 
     @property
@@ -389,7 +408,7 @@ class Batch:
     def admit(self, params: Params, rho, umax_tol: float, max_steps: int):
         """Returns the case id, or None when the batch is full (ENOMEM)."""
         rho = np.ascontiguousarray(rho, dtype=np.float64)
-        assert rho.shape == (params.ny, params.nx)
+        _require(rho.shape == (params.ny, params.nx), "rho must have shape (ny, nx)")
         cp = params.c()
         cid = ctypes.c_int64()
         st = self._check(self.lib.wblbe_batch_admit(self.h, ctypes.byref(cp),
