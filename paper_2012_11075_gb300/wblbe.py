@@ -372,11 +372,21 @@ class Batch:
             raise WblbeError(st, self.lib.wblbe_batch_last_error(None).decode())
         self.h = h
         self.scheme, self.precision = scheme, precision
+        self._shapes = {}                      # case id -> (ny, nx) of an admitted case
 
     def _check(self, st, allow=(OK,)):
         if st not in allow:
             raise WblbeError(st, self.lib.wblbe_batch_last_error(self.h).decode())
         return st
+
+    def _shape_of(self, case_id: int, shape):
+        """The case's (ny, nx); a shape given by the caller must match it."""
+        known = self._shapes.get(int(case_id))
+        if known is None:
+            raise WblbeError(EINVAL, f"unknown case {case_id}")
+        if shape is not None:
+            _require(tuple(shape) == known, f"case {case_id} has shape {known}")
+        return known
 
     def close(self):
         if getattr(self, "h", None):
@@ -415,7 +425,10 @@ class Batch:
                                                     ctypes.c_void_p(rho.ctypes.data),
                                                     float(umax_tol), int(max_steps),
                                                     ctypes.byref(cid)), allow=(OK, ENOMEM))
-        return None if st == ENOMEM else int(cid.value)
+        if st == ENOMEM:
+            return None
+        self._shapes[int(cid.value)] = (params.ny, params.nx)
+        return int(cid.value)
 
     def advance(self, launches: int = 1):
         self._check(self.lib.wblbe_batch_advance(self.h, int(launches)))
@@ -432,22 +445,23 @@ class Batch:
         return {"case_id": ci.case_id, "state": ci.state, "steps": ci.steps,
                 "stats": ci.stats.as_dict()}
 
-    def fetch(self, case_id: int, shape):
-        outs = [np.empty(shape) for _ in range(4)]
+    def fetch(self, case_id: int, shape=None):
+        outs = [np.empty(self._shape_of(case_id, shape)) for _ in range(4)]
         st = CStats()
         self._check(self.lib.wblbe_batch_fetch(self.h, int(case_id),
                                                *[ctypes.c_void_p(o.ctypes.data) for o in outs],
                                                ctypes.byref(st)))
         return dict(zip(("rho", "ux", "uy", "mu"), outs)), st.as_dict()
 
-    def get_populations(self, case_id: int, shape) -> np.ndarray:
-        f = np.empty((9,) + tuple(shape))
+    def get_populations(self, case_id: int, shape=None) -> np.ndarray:
+        f = np.empty((9,) + self._shape_of(case_id, shape))
         self._check(self.lib.wblbe_batch_get_populations(self.h, int(case_id),
                                                          ctypes.c_void_p(f.ctypes.data)))
         return f
 
     def retire(self, case_id: int):
         self._check(self.lib.wblbe_batch_retire(self.h, int(case_id)))
+        self._shapes.pop(int(case_id), None)
 
     def counts(self) -> dict:
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
