@@ -47,8 +47,9 @@ def stability_map(ratios=(2.0, 5.0, 10.0, 20.0, 50.0),
     until it becomes non-finite) and return one record per case:
     {rho0_mode, rho0, ratio, tau, state ('stable' or 'unstable'), steps,
     umax, mass}.  ``steps`` is rounded up to whole launches.  Growth near
-    the stability limit is slow (the WB droplet at tau = 0.8 stays finite
-    for 20000 steps and fails near 25000-30000), hence the default."""
+    the stability limit is slow (the WB droplet at tau = 0.8, W = 4, fails
+    only between steps 15000 and 30000, depending on the density ratio),
+    hence the default."""
     cases = grid(ratios, taus, rho0_modes)
     params = []
     for mode, ratio, tau in cases:
