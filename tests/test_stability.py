@@ -124,3 +124,50 @@ def test_wb_flat_interface_transverse_mode(tau, grows):
         assert a1 > 1e3 * a0, (a0, a1)
     else:
         assert a1 < a0, (a0, a1)
+
+
+def _amplification(o, f0, mx, my, eps=1e-6):
+    """9 x 9 amplification matrix of the oracle's step linearised about the
+    uniform state f0, for the lattice wave number 2 pi (mx, my) / n: the
+    responses to cos and sin perturbations of each population (central
+    differences), read at node (0, 0)."""
+    n = f0.shape[1]
+    y, x = np.mgrid[0:n, 0:n]
+    ph = 2 * np.pi * (mx * x + my * y) / n
+    G = np.zeros((9, 9), complex)
+    for i in range(9):
+        parts = []
+        for wave in (np.cos(ph), np.sin(ph)):
+            fp, fm = f0.copy(), f0.copy()
+            fp[i] += eps * wave
+            fm[i] -= eps * wave
+            o.step(fp, 1)
+            o.step(fm, 1)
+            parts.append((fp - fm)[:, 0, 0] / (2 * eps))
+        G[:, i] = parts[0] + 1j * parts[1]
+    return G
+
+
+@pytest.mark.parametrize("scheme_name,tau,unstable", [("wb", 0.80, True), ("wb", 0.90, False),
+                                                      ("standard", 0.60, False)])
+def test_bulk_linear_stability(scheme_name, tau, unstable):
+    """von Neumann analysis of the oracle's step about a uniform bulk state
+    (liquid, ratio 10, W = 4, kappa = 0.01) on a 64^2 lattice, along
+    k = (pi, k_y).  The WB scheme amplifies the x-alternating density mode
+    with a slow modulation in y for tau below about 0.854 (at tau = 0.8 by
+    about 5e-4 per step, the growth seen at the slab's interfaces); at
+    tau = 0.9 every mode is bounded.  The standard scheme, whose equilibrium
+    carries the pressure, shows no such mode."""
+    from oracle import equilibrium as eq
+    from oracle.oracle import STANDARD, WELL_BALANCED, Oracle, Params
+    n, kappa, width = 64, 0.01, 4.0
+    beta = eq.beta_for_width(kappa, width, 1.0, 0.1)
+    scheme = WELL_BALANCED if scheme_name == "wb" else STANDARD
+    o = Oracle(Params(n, n, tau, kappa, beta, 1.0, 0.1, 0.0, scheme))
+    f0 = o.init(np.full((n, n), 1.0))
+    growth = max(np.abs(np.linalg.eigvals(_amplification(o, f0, n // 2, my))).max() - 1.0
+                 for my in (1, 2, 3, 4, 6, 8))
+    if unstable:
+        assert growth > 1e-4, growth
+    else:
+        assert growth < 1e-8, growth
