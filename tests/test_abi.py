@@ -126,3 +126,38 @@ def test_workspace_too_small_is_enomem():
                           ctypes.byref(h))
     assert st == wblbe.ENOMEM and not h.value
     assert b"needs" in lib.wblbe_last_error(None)
+
+
+def test_batch_host_side_validation():
+    """Batch sizes, case sizes, configurations and NULL handles are checked on
+    the host, before any device work."""
+    lib = wblbe.load_library()
+    assert lib.wblbe_batch_workspace_bytes(0, 64, 4096, 1 << 20) == 0
+    assert lib.wblbe_batch_workspace_bytes(4, 0, 4096, 1 << 20) == 0
+    assert lib.wblbe_batch_workspace_bytes(4, 64, 63, 1 << 20) == 0
+    ok = lib.wblbe_batch_workspace_bytes(4, 64, 4096, 1 << 20)
+    assert ok > (1 << 20) and ok % 256 == 0
+    small = _params(nx=7, ny=64).c()
+    assert lib.wblbe_batch_case_bytes(ctypes.byref(small)) == 0      # nx < 8
+    case = _params(nx=64, ny=48, precision=wblbe.FP32_SHIFTED).c()
+    assert lib.wblbe_batch_case_bytes(ctypes.byref(case)) >= 2 * 9 * 64 * 48 * 4
+    h = ctypes.c_void_p()
+    for cfg in (wblbe.CBatchConfig(96, 32, 1), wblbe.CBatchConfig(128, 2, 1),
+                wblbe.CBatchConfig(128, 32, 0)):
+        st = lib.wblbe_batch_create(wblbe.WELL_BALANCED, wblbe.FP32_SHIFTED, 4, 64, 4096,
+                                    ctypes.c_void_p(256), ok, None, ctypes.byref(cfg),
+                                    ctypes.byref(h))
+        assert st == wblbe.EINVAL and not h.value
+    cfg = wblbe.CBatchConfig(128, 32, 1)
+    st = lib.wblbe_batch_create(wblbe.WELL_BALANCED, 7, 4, 64, 4096, ctypes.c_void_p(256), ok,
+                                None, ctypes.byref(cfg), ctypes.byref(h))
+    assert st == wblbe.EINVAL                                          # unknown precision
+    st = lib.wblbe_batch_create(wblbe.WELL_BALANCED, wblbe.FP64, 4, 64, 4096,
+                                ctypes.c_void_p(100), ok, None, ctypes.byref(cfg),
+                                ctypes.byref(h))
+    assert st == wblbe.EINVAL and b"aligned" in lib.wblbe_batch_last_error(None)
+    n = ctypes.c_int32()
+    assert lib.wblbe_batch_advance(None, 1) == wblbe.EINVAL
+    assert lib.wblbe_batch_poll(None, None, 0, ctypes.byref(n)) == wblbe.EINVAL
+    assert lib.wblbe_batch_retire(None, 0) == wblbe.EINVAL
+    assert lib.wblbe_batch_destroy(None) == wblbe.EINVAL
