@@ -171,3 +171,28 @@ def test_bulk_linear_stability(scheme_name, tau, unstable):
         assert growth > 1e-4, growth
     else:
         assert growth < 1e-8, growth
+
+
+@pytest.mark.parametrize("tau", [0.7, 0.8, 0.9, 1.2])
+def test_bulk_mode_matches_second_order_formula(tau):
+    """Linearised about a uniform rest state, the WB amplification matrix at
+    k = (pi, 0) has the simple eigenvalue 1 (the x-alternating density field,
+    which feels no force).  Second-order perturbation in the modulation
+    k_y = q gives
+        lambda = 1 + S (w^2 - 8 w + 8) / (6 w (w - 2)) q^2 + O(q^4),
+    w = 1/tau, S = rho (psi_0''(rho) + 4 kappa): growth for w > 4 - 2 sqrt 2,
+    i.e. tau < (2 + sqrt 2) / 4, whatever the free energy.  The oracle's
+    eigenvalue at q = 2 pi / 128 agrees with it to 1 %."""
+    from oracle import equilibrium as eq
+    from oracle.oracle import WELL_BALANCED, Oracle, Params
+    n, kappa, width, rho = 128, 0.01, 4.0, 1.0
+    beta = eq.beta_for_width(kappa, width, 1.0, 0.1)
+    o = Oracle(Params(n, n, tau, kappa, beta, 1.0, 0.1, 0.0, WELL_BALANCED))
+    f0 = o.init(np.full((n, n), rho))
+    lam = np.linalg.eigvals(_amplification(o, f0, n // 2, 1))
+    got = lam[np.argmin(np.abs(lam - 1.0))] - 1.0
+    w, q = 1.0 / tau, 2 * np.pi / n
+    S = rho * (eq.dmu0(rho, beta, 1.0, 0.1) + 4 * kappa)
+    want = S * (w * w - 8 * w + 8) / (6 * w * (w - 2)) * q * q
+    assert abs(got.imag) < 1e-12
+    assert abs(got.real - want) < 0.01 * abs(want), (got, want)
