@@ -86,7 +86,12 @@ enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1, WBLBE_STANDARD_PRESSURE = 2,
  *   (standard: s_i = w_i rho_ref; well-balanced: s_0 = rho_ref - (1-w_0) rho0,
  *   s_i = w_i rho0), arithmetic in float32, reductions in float64.  The shift
  *   is exact in real arithmetic: sum_i s_i = rho_ref and a uniform s_i is
- *   invariant under streaming. */
+ *   invariant under streaming.  Near a steady state the float32 rounding
+ *   repeats from step to step, so its small biases add up: the mass drifts
+ *   (about 1e-4 relative per 1e5 steps on a 256^2 droplet), interfaces drift,
+ *   and max|u| settles near 1e-6.  Bulk densities and the Laplace jump stay
+ *   close to FP64 (1e-5, 0.3 %).  Equilibria at round-off velocity need
+ *   WBLBE_FP64. */
 enum { WBLBE_FP64 = 0, WBLBE_FP32_SHIFTED = 1 };
 
 /* The paper's statement of the problem (Sec. IV): lattice nx x ny (periodic),
