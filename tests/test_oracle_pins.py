@@ -533,3 +533,26 @@ def test_e6_gradient_exact_on_quadratics_and_more_isotropic():
     # measured: 2.3e-4 (9-point) and 3.9e-6 (E6)
     assert aniso["e4"] > 1e-4
     assert aniso["e6"] < 0.05 * aniso["e4"]
+
+
+@pytest.mark.parametrize("radius,tol", [(40.0, 0.05), (60.0, 0.02)])
+def test_oracle_droplet_obeys_laplace_law(radius, tol):
+    """The oracle's stationary droplets after 100000 WB steps (stored by
+    tests/golden/make_oracle_droplets.py, which calls only the oracle):
+    the bulk pressure jump p_0(rho_in) - p_0(rho_out) equals the 2D
+    Young-Laplace value sigma / R up to the O(W/R) curvature correction,
+    both bulk densities sit above saturation (Sec. IV.B), the mass is the
+    initial mass, and the row through the centre is mirror-symmetric."""
+    from paper_2012_11075_gb300 import workloads as wl
+    with open(os.path.join(os.path.dirname(GOLDEN), "oracle_droplets_100k.json")) as fh:
+        gold = json.load(fh)
+    c = gold["cases"][f"R{int(radius)}"]
+    pr = wl.droplet(n=256, radius=radius, tau=1.0)
+    sigma = eq.surface_tension(pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
+    dp = eq.p0(c["rho_in"], pr.beta, pr.rho_l, pr.rho_g) - \
+        eq.p0(c["rho_out"], pr.beta, pr.rho_l, pr.rho_g)
+    assert abs(dp * radius / sigma - 1.0) < tol
+    assert c["rho_in"] > pr.rho_l and c["rho_out"] > pr.rho_g
+    assert abs(c["mass"] - pr.rho.sum()) < 1e-12 * pr.rho.sum()
+    row = np.array(c["rho_row128"])
+    assert np.max(np.abs(row[1:] - row[1:][::-1])) < 1e-12      # x -> 256 - x about x = 128
