@@ -196,3 +196,20 @@ def test_bulk_mode_matches_second_order_formula(tau):
     want = S * (w * w - 8 * w + 8) / (6 * w * (w - 2)) * q * q
     assert abs(got.imag) < 1e-12
     assert abs(got.real - want) < 0.01 * abs(want), (got, want)
+
+
+def test_bulk_mode_formula_is_derived():
+    """The formula pinned above, derived symbolically from the linearised
+    update (tests/bulk_mode_derivation.py, which shares no code with the
+    oracle or the CUDA path): at k = (pi, q) the eigenvalue 1 moves by
+    S (w^2 - 8 w + 8) / (6 w (w - 2)) q^2, which changes sign at
+    w = 4 -+ 2 sqrt 2, and the eigenvalue -1 shrinks in modulus for w < 2."""
+    sp = pytest.importorskip("sympy")
+    from tests import bulk_mode_derivation as d
+    om, S, lam1, lam2, a2 = d.second_order(1)
+    assert lam1 == 0
+    assert sp.simplify(lam2 - S * (om ** 2 - 8 * om + 8) / (6 * om * (om - 2))) == 0
+    roots = sorted(sp.solve(sp.Eq(a2, 0), om), key=lambda r: float(r))
+    assert [sp.nsimplify(r) for r in roots] == [4 - 2 * sp.sqrt(2), 4 + 2 * sp.sqrt(2)]
+    om, S, lam1, lam2, a2 = d.second_order(-1)
+    assert lam1 == 0 and sp.simplify(a2 - (om - 2) / (3 * om)) == 0
