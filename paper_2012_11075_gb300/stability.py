@@ -11,16 +11,39 @@ velocity) or after how many steps it became non-finite.
 Every case: an n x n periodic lattice, one droplet of radius n/4 at the
 centre with the tanh profile of Eq. Tanh, rho_l = 1, rho_g = 1/ratio,
 interface width W (beta = 8 kappa / (W (rho_l - rho_g))^2).
+
+The linear limit the map runs into is known in closed form.  Linearised
+about a uniform rest state, the well-balanced update (Eq. mFeq, Eq. mFi,
+BGK, streaming) leaves the density field that alternates along one lattice
+axis (wave number pi) neutral: its central gradients vanish.  With a slow
+modulation q along the other axis its eigenvalue becomes
+1 + S (w^2 - 8 w + 8) / (6 w (w - 2)) q^2 + O(q^4), w = 1/tau,
+S = rho (psi_0''(rho) + 4 kappa).  It grows for tau < (2 + sqrt 2) / 4,
+whatever the free energy.
 """
 from __future__ import annotations
 
 import itertools
+import math
 
 from . import workloads as wl
 from .wblbe import FP64, WELL_BALANCED, Batch, Params
 
 RHO0_MODES = ("zero", "gas", "mean")
 STATE_NAMES = {1: "converged", 2: "stable", 3: "unstable"}
+
+# relaxation time below which the well-balanced scheme has a growing bulk mode
+WB_TAU_LIMIT = 0.5 + math.sqrt(2.0) / 4.0
+
+
+def bulk_mode_growth(tau: float, rho: float, d2psi: float, kappa: float, q: float) -> float:
+    """|lambda| - 1 per step of the well-balanced bulk mode that alternates
+    along one axis and is modulated with wave number q along the other, to
+    second order in q, about a uniform rest state of density rho
+    (d2psi = psi_0''(rho)).  Positive means growth."""
+    w = 1.0 / tau
+    s = rho * (d2psi + 4.0 * kappa)
+    return s * (w * w - 8.0 * w + 8.0) / (6.0 * w * (w - 2.0)) * q * q
 
 
 def rho0_value(mode: str, rho_l: float, rho_g: float) -> float:
