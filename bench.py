@@ -25,6 +25,7 @@ import hashlib
 import json
 import math
 import os
+import ctypes
 import statistics
 import subprocess
 import sys
@@ -41,6 +42,12 @@ UNIT = "MLUPS"
 WORKLOAD = "large_domain_4096x4096_64droplets_ratio10_wb"
 BYTES_PER_LU = {"f32": 72, "f64": 144}          # 9 reads + 9 writes per node update
 SUBSTEPS = {"f32": 200, "f64": 40}              # lattice steps per benchmark step
+# FP64 flops per lattice update of the FP64 step kernel, from the ncu
+# instruction mix (2 x DFMA + DADD + DMUL per node, halo work included)
+FP64_FLOPS_PER_LU = 178
+# oldest state (lattice steps since initialisation) a timed step may start
+# from; see time_device
+MAX_STATE_AGE = 1200
 PROFILE_JSON = ROOT / "profiles" / "lbm_step_traffic.json"
 KERNEL_SOURCES = [ROOT / "paper_2012_11075_gb300" / "csrc" / "lbm_kernels.cuh"]
 
@@ -138,9 +145,9 @@ def max_over_ranks(world, value: float, device=None) -> float:
     return float(t.item())
 
 
-def make_problem(n=4096):
+def make_problem(n=4096, ratio=10.0):
     from paper_2012_11075_gb300 import workloads as wl
-    return wl.large_domain(n=n, count=64, ratio=10.0, width=5.0, kappa=0.01, tau=0.7)
+    return wl.large_domain(n=n, count=64, ratio=ratio, width=5.0, kappa=0.01, tau=0.7)
 
 
 # ---------------------------------------------------------------------------------
@@ -217,26 +224,80 @@ def cpu_baseline_all_cores(pr, seconds_target=10.0):
                       f"lattice, OpenMP over rows on {threads} threads"}
 
 
-def time_device(solver, substeps, steps, warmup, stream, torch):
-    """Device-resident timing: K x (S lattice steps + stats pass).  Returns
-    total seconds, seconds in the step kernels, launches."""
+def time_device(solver, substeps, steps, warmup, stream, torch, rho_dev=None,
+                max_age=MAX_STATE_AGE):
+    """Device-resident timing of K benchmark steps, each S lattice steps and
+    one stats pass, bracketed by CUDA events on the launching stream.
+
+    The state is never older than max_age lattice steps: before a benchmark
+    step that would take it past that age it is re-initialised from the
+    device-resident density rho_dev, outside the event window (the
+    large-domain case at tau = 0.7 becomes non-finite between lattice steps
+    2000 and 5000, whatever the precision).  Returns total seconds inside
+    the windows, seconds in the step kernels, kernel launches inside the
+    windows and the health record (lattice age at the start of every timed
+    step, and whether any timed step ended on a non-finite state)."""
+    def renew():
+        if rho_dev is not None and solver.steps + substeps > max_age:
+            solver.init_rho(rho_dev)            # synchronises; outside the window
+
     for _ in range(warmup):
+        renew()
         solver.step(substeps)
         solver.stats()
     torch.cuda.synchronize()
-    l0 = solver.kernel_launches
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps + 1)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    ages, bad, launches = [], [], 0
     with torch.cuda.stream(stream):
-        ev[0].record(stream)
         for k in range(steps):
+            renew()
+            ages.append(int(solver.steps))
+            l0 = solver.kernel_launches
+            ev[k][0].record(stream)
             solver.step(substeps)
-            ev[2 * k + 1].record(stream)
-            solver.stats()                      # synchronises: the step's result
-            ev[2 * k + 2].record(stream)
+            ev[k][1].record(stream)
+            st = solver.stats()                 # synchronises: the step's result
+            ev[k][2].record(stream)
+            launches += solver.kernel_launches - l0
+            bad.append(bool(st["nonfinite"]))
     torch.cuda.synchronize()
-    total = ev[0].elapsed_time(ev[-1]) / 1e3
-    kern = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(steps)) / 1e3
-    return total, kern, solver.kernel_launches - l0
+    total = sum(e[0].elapsed_time(e[2]) for e in ev) / 1e3
+    kern = sum(e[0].elapsed_time(e[1]) for e in ev) / 1e3
+    health = {"max_state_age": max_age, "state_age_at_timed_steps": ages,
+              "nonfinite": any(bad)}
+    return total, kern, launches, health
+
+
+def measure_fp64_peak(stream, torch, blocks_per_sm=8, threads=256, iters=16384, reps=5):
+    """The device's FP64 fused multiply-add rate (TFLOP/s, 2 flops per FMA)
+    from the library's probe kernel: eight independent FMA chains per
+    thread, a full-occupancy grid; best of reps launches by CUDA events,
+    SM clocks sampled meanwhile."""
+    from paper_2012_11075_gb300 import wblbe
+    lib = wblbe.load_library()
+    dev = torch.cuda.current_device()
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * blocks_per_sm
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    for _ in range(2):
+        assert lib.wblbe_probe_fp64_fma(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters,
+                                        sp) == wblbe.OK
+    torch.cuda.synchronize()
+    best = float("inf")
+    with ClockSampler(dev) as clk:
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lib.wblbe_probe_fp64_fma(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters, sp)
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b) / 1e3)
+    flops = blocks * threads * iters * 8 * 2
+    assert bool(torch.isfinite(out).all())
+    return {"tflops": flops / best / 1e12, "unit": "TFLOP/s", "launch_ms": best * 1e3,
+            "how": f"{blocks} CTAs x {threads} threads x {iters} iterations x 8 independent "
+                   f"DFMA chains, best of {reps} launches (CUDA events)",
+            "clocks": clk.summary()}
 
 
 def time_e2e(solver, rho_pinned, rho_out_pinned, substeps, steps, warmup, torch):
@@ -373,7 +434,7 @@ def run_schemes(args, stream, torch):
                                   scheme=sch, precision=prec)
             solver = wblbe.Solver(params, stream=stream)
             solver.init_rho(pr.rho)
-            total, kern, _ = time_device(solver, S, 2, 1, stream, torch)
+            total, kern, _, _ = time_device(solver, S, 2, 1, stream, torch)
             st = solver.stats()
             kern_avg = kern / (2 * S)
             out["results"][f"{prec_name}/{name}"] = {
@@ -408,31 +469,38 @@ def run_ours(args, world, rank, local):
             print(json.dumps({"batched": run_batched(args, stream, torch)}), flush=True)
         return 0
     results = {}
-    precisions = [("f32", wblbe.FP32_SHIFTED), ("f64", wblbe.FP64)]
+    precisions = [("f32", wblbe.FP32_SHIFTED, pr), ("f64", wblbe.FP64, pr)]
     if args.only != "both":
         precisions = [x for x in precisions if x[0] == args.only]
-    for prec_name, prec in precisions:
-        params = wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g,
-                              scheme=wblbe.WELL_BALANCED, precision=prec)
+    elif not args.no_ratio50:
+        # the same large-domain case at density ratio 50 (rho_g = 0.02)
+        precisions.insert(1, ("f32_ratio50", wblbe.FP32_SHIFTED, make_problem(args.lattice, 50.0)))
+    for prec_name, prec, prob in precisions:
+        params = wblbe.Params(prob.nx, prob.ny, prob.tau, prob.kappa, prob.beta, prob.rho_l,
+                              prob.rho_g, scheme=wblbe.WELL_BALANCED, precision=prec)
         solver = wblbe.Solver(params, stream=stream)
-        solver.init_rho(pr.rho)
-        S = SUBSTEPS[prec_name]
-        K = args.steps if prec_name == "f32" else max(1, min(args.steps, 5))
+        rho_dev = torch.from_numpy(prob.rho).to(dev)
+        solver.init_rho(rho_dev)
+        bpl = BYTES_PER_LU["f64" if prec == wblbe.FP64 else "f32"]
+        S = SUBSTEPS["f64" if prec == wblbe.FP64 else "f32"]
+        K = args.steps if prec != wblbe.FP64 else max(1, min(args.steps, 5))
         barrier(world)
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
-            total, kern, launches = time_device(solver, S, K, args.warmup, stream, torch)
+            total, kern, launches, health = time_device(solver, S, K, args.warmup, stream, torch,
+                                                        rho_dev=rho_dev)
         total = max_over_ranks(world, total, dev)
         st = solver.stats()
-        lu = pr.nx * pr.ny * S * K
+        lu = prob.nx * prob.ny * S * K
         step_launches = S * K
         kern_avg = kern / step_launches
-        achieved_gbs = BYTES_PER_LU[prec_name] * pr.nx * pr.ny / kern_avg / 1e9
+        achieved_gbs = bpl * prob.nx * prob.ny / kern_avg / 1e9
+        health.update(umax=st["umax"], mass_drift_rel=st["mass_drift_rel"])
         results[prec_name] = dict(
             mlups=lu * world / total / 1e6, total=total, kern_avg=kern_avg,
+            kern_mlups=prob.nx * prob.ny / kern_avg / 1e6,
             achieved_gbs=achieved_gbs, launches=launches, clocks=clk.summary(),
-            launch=solver.get_launch(), umax=st["umax"], mass_drift=st["mass_drift_rel"],
-            nonfinite=st["nonfinite"], S=S, K=K)
+            launch=solver.get_launch(), health=health, S=S, K=K)
         if prec_name == "f32" and not args.no_e2e:
             rho_pinned = torch.from_numpy(pr.rho).pin_memory()
             rho_out = torch.empty_like(rho_pinned).pin_memory()
@@ -457,10 +525,10 @@ def run_ours(args, world, rank, local):
         prof = json.loads(PROFILE_JSON.read_text())
         if prof.get("kernel_hash") == kernel_hash():
             traffic = prof.get("dram_bytes_per_launch_full_size")
-    fp64_peak_tflops = 1.25                       # nominal GB300 FP64 rate (FMA = 2 flops)
+    fp64_peak = measure_fp64_peak(stream, torch)
     # FP64 flops per lattice update, measured with ncu on the FP64 step kernel
     # (2 x DFMA + DADD + DMUL per node, 2048^2 case, halo work included)
-    fp64_flops_per_lu = 178
+    fp64_flops_per_lu = FP64_FLOPS_PER_LU
     line = {
         "metric": METRIC, "value": r32["mlups"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -488,15 +556,27 @@ def run_ours(args, world, rank, local):
                  "steps": r64["K"],
                  "roofline_hbm": {"achieved": r64["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                                   "frac": r64["achieved_gbs"] / hbm_peak},
-                 "roofline_alu": {"bound": "alu", "achieved": r64["mlups"] * 1e6 * fp64_flops_per_lu / 1e12,
-                                  "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                                  "frac": r64["mlups"] * 1e6 * fp64_flops_per_lu / 1e12 / fp64_peak_tflops},
+                 "roofline_alu": {"bound": "alu",
+                                  "achieved": r64["kern_mlups"] * 1e6 * fp64_flops_per_lu / 1e12,
+                                  "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                                  "frac": r64["kern_mlups"] * 1e6 * fp64_flops_per_lu / 1e12
+                                  / fp64_peak["tflops"],
+                                  "flops_per_lattice_update": fp64_flops_per_lu,
+                                  "peak_source": "of measured (FP64 FMA probe kernel, this run)",
+                                  "peak_measurement": fp64_peak},
                  "gpu_launches": r64["launches"], "clocks": r64["clocks"]},
-        "health": {"f32_lattice_steps": (args.warmup + r32["K"]) * r32["S"],
-                   "f32_umax": r32["umax"], "f32_mass_drift_rel": r32["mass_drift"],
-                   "f64_umax": r64["umax"], "f64_mass_drift_rel": r64["mass_drift"],
-                   "nonfinite": bool(r32["nonfinite"] or r64["nonfinite"])},
+        "health": {k: v["health"] for k, v in results.items() if "health" in v},
     }
+    line["health"]["nonfinite"] = any(h["nonfinite"] for h in line["health"].values())
+    if "f32_ratio50" in results:
+        r50 = results["f32_ratio50"]
+        line["ratio50"] = {
+            "workload": WORKLOAD.replace("ratio10", "ratio50"), "value": r50["mlups"],
+            "unit": UNIT, "lattice_steps_per_step": r50["S"], "steps": r50["K"],
+            "roofline": {"bound": "hbm", "achieved": r50["achieved_gbs"], "peak": hbm_peak,
+                         "unit": "GB/s", "frac": r50["achieved_gbs"] / hbm_peak,
+                         "peak_source": peak_note, "kernel_ms": r50["kern_avg"] * 1e3},
+            "gpu_launches": r50["launches"], "clocks": r50["clocks"]}
     if not args.no_schemes:
         line["schemes"] = run_schemes(args, stream, torch)
     if not args.no_batched:
@@ -506,6 +586,9 @@ def run_ours(args, world, rank, local):
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(pr)
     print(json.dumps(line), flush=True)
+    if line["health"]["nonfinite"]:
+        print("bench: a timed step ended on a non-finite state", file=sys.stderr, flush=True)
+        return 1
     return 0
 
 
@@ -524,6 +607,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-ratio50", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
     ap.add_argument("--serve-window", type=float, default=5.0)

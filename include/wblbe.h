@@ -312,9 +312,9 @@ const char* wblbe_batch_last_error(wblbe_batch_handle b);
 
 /* ---- allocation-free statistics pass ------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
- * cannot allocate device memory at all: code running while a CUDA graph is
- * being captured, hosts whose own allocator owns the whole device and
- * forbids cudaMalloc, plug-ins that only receive buffers.  It computes, from
+ * cannot allocate device memory at all: hosts whose own allocator has
+ * reserved the whole device and forbids cudaMalloc, and plug-ins or
+ * callbacks that only ever receive buffers.  It computes, from
  * caller-held populations f ([9][ny][nx] float64 on the device, the layout of
  * wblbe_get_populations), the fields rho, ux, uy, mu ([ny][nx] float64 device
  * pointers, each may be NULL) and the stats (host pointer, may be NULL;
@@ -340,6 +340,18 @@ wblbe_status wblbe_moments_noalloc(const wblbe_params* params, const double* f,
                                    double* mu, wblbe_stats* stats,
                                    void* cuda_stream);
 const char* wblbe_noalloc_last_error(void);
+
+/* Measurement aid (no counterpart in the paper): the device's float64
+ * fused multiply-add rate, the ceiling of the float64 step kernel, which is
+ * bound by FP64 arithmetic rather than by memory traffic.  Launches
+ * `blocks` CTAs of `threads` threads (a multiple of 32, at most 1024); each
+ * thread runs 8 independent chains of `iters` fused multiply-adds and
+ * writes one float64 to out (a device array of blocks * threads doubles,
+ * owned by the caller).  One launch performs blocks * threads * iters * 8
+ * FMAs (2 flops each).  Asynchronous on cuda_stream; the caller times it.
+ * EINVAL on bad arguments, ECUDA if the launch fails. */
+wblbe_status wblbe_probe_fp64_fma(double* out, int32_t blocks, int32_t threads,
+                                  int32_t iters, void* cuda_stream);
 
 /* Debugging aid (no counterpart in the paper).  Compute-sanitizer is not
  * available where this library is tested, so a build with

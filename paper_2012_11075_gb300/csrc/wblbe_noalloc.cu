@@ -1,11 +1,10 @@
 // Allocation-free moments/statistics entry point (wblbe_moments_noalloc).
 //
-// Some callers cannot allocate device memory at all: code that runs while a
-// CUDA graph is being captured, hosts that pre-reserve the whole device for
-// another allocator and forbid cudaMalloc, or plug-ins that only ever see
-// buffers handed to them.  For them this file keeps the only scratch the
-// statistics reduction needs (one record per CTA plus the final record) in a
-// file-scope __device__ array of fixed size.  Every GPU that loads the
+// Some callers cannot allocate device memory at all: hosts that pre-reserve
+// the whole device for another allocator and forbid cudaMalloc, or plug-ins
+// and callbacks that only ever see buffers handed to them.  For them this
+// file keeps the only scratch the statistics reduction needs (one record per
+// CTA plus the final record) in a file-scope __device__ array of fixed size.  Every GPU that loads the
 // library holds that array until the process exits.
 //
 // The caller passes the populations f_i(x, t) (float64, [9][ny][nx], the

@@ -125,6 +125,8 @@ _SIGNATURES = {
                                              ctypes.POINTER(CStats), _P]),
     "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
     "wblbe_debug_bounds_errors": (ctypes.c_uint, [ctypes.c_int32]),
+    "wblbe_probe_fp64_fma": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            _P]),
 }
 
 _lib = None

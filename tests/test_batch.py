@@ -82,8 +82,8 @@ def test_batch_fp64_matches_oracle():
     for pr, cid in zip(cases, ids):
         fo, mo, so = run_oracle(pr, WELL_BALANCED, 200)
         fg = b.get_populations(cid, (pr.ny, pr.nx))
-        glob, _ = pop_error(fg, fo)
-        assert glob < 1e-12, (pr.name, glob)
+        glob, per = pop_error(fg, fo)
+        assert glob < 1e-12 and per < 1e-12, (pr.name, glob, per)
         m, st = b.fetch(cid, (pr.ny, pr.nx))
         assert np.max(np.abs(m["rho"] - mo["rho"])) < 1e-12
         assert st["mass"] == pytest.approx(so["mass"], rel=1e-13)
