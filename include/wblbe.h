@@ -196,6 +196,14 @@ wblbe_status wblbe_set_populations(wblbe_handle h, const double* f,
 int64_t wblbe_step_count(wblbe_handle h);
 int64_t wblbe_kernel_launches(wblbe_handle h);
 
+/* Set the step counter (>= 0), e.g. after wblbe_set_populations when
+ * resuming a checkpoint.  In WBLBE_FP32_SHIFTED storage with the
+ * well-balanced scheme the counter also seeds the stochastic rounding of the
+ * rest population (see WBLBE_FP32_SHIFTED), so a resumed run that restores
+ * it repeats the rounding decisions of the run it continues.  EINVAL on a
+ * NULL handle or a negative step. */
+wblbe_status wblbe_set_step_count(wblbe_handle h, int64_t step);
+
 /* Release the handle (the workspace stays the caller's).  NULL -> EINVAL.
  * Synchronises the stream first. */
 wblbe_status wblbe_destroy(wblbe_handle h);

@@ -29,6 +29,8 @@ BUILD_DIR = HERE / "_build"
 LIB_PATH = BUILD_DIR / f"liboracle_{platform.machine()}.so"
 # timing-only build with the row loops split over threads (same arithmetic)
 LIB_OMP_PATH = BUILD_DIR / f"liboracle_omp_{platform.machine()}.so"
+# rounding-sensitivity build: the density summed in another order (tests only)
+LIB_PAIRWISE_PATH = BUILD_DIR / f"liboracle_pairwise_{platform.machine()}.so"
 
 STANDARD = 0
 WELL_BALANCED = 1
@@ -44,17 +46,21 @@ CY = (0, 0, 1, 0, -1, 1, 1, -1, -1)
 W = (4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36)
 
 
-def build(force: bool = False, openmp: bool = False) -> Path:
+def build(force: bool = False, openmp: bool = False, pairwise_density: bool = False) -> Path:
     """Compile the C oracle (plain gcc, no FMA contraction) if needed.
     ``openmp`` builds the timing-only variant whose row loops run on all
-    host threads; every node is computed as in the serial build."""
+    host threads; every node is computed as in the serial build.
+    ``pairwise_density`` builds the rounding-sensitivity variant that sums
+    rho = sum_i f_i in pairs (nothing else differs)."""
+    assert not (openmp and pairwise_density)
     BUILD_DIR.mkdir(exist_ok=True)
-    path = LIB_OMP_PATH if openmp else LIB_PATH
+    path = LIB_OMP_PATH if openmp else (LIB_PAIRWISE_PATH if pairwise_density else LIB_PATH)
     if force or not path.exists() or path.stat().st_mtime < SRC.stat().st_mtime:
         tmp = path.with_suffix(f".{os.getpid()}.tmp")
         subprocess.check_call(
             ["gcc", "-O3", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
              *(["-fopenmp"] if openmp else []),
+             *(["-DORC_DENSITY_PAIRWISE"] if pairwise_density else []),
              "-fPIC", "-shared", "-o", str(tmp), str(SRC), "-lm"])
         os.replace(tmp, path)
     return path
@@ -77,9 +83,10 @@ class _Stats(ctypes.Structure):
 _libs = {}
 
 
-def _load(openmp: bool = False):
-    if openmp not in _libs:
-        lib = ctypes.CDLL(str(build(openmp=openmp)))
+def _load(openmp: bool = False, pairwise_density: bool = False):
+    key = (openmp, pairwise_density)
+    if key not in _libs:
+        lib = ctypes.CDLL(str(build(openmp=openmp, pairwise_density=pairwise_density)))
         dp = ctypes.POINTER(ctypes.c_double)
         pp = ctypes.POINTER(_Params)
         for name in ("orc_psi0", "orc_mu0", "orc_p0"):
@@ -96,8 +103,8 @@ def _load(openmp: bool = False):
         lib.orc_step.argtypes = [pp, dp, ctypes.c_long]
         lib.orc_step.restype = ctypes.c_int
         lib.orc_stats_of.argtypes = [pp, dp, ctypes.POINTER(_Stats)]
-        _libs[openmp] = lib
-    return _libs[openmp]
+        _libs[key] = lib
+    return _libs[key]
 
 
 def _ptr(a: np.ndarray):
@@ -128,12 +135,15 @@ class Params:
 class Oracle:
     """FP64 CPU oracle bound to one parameter set."""
 
-    def __init__(self, params: Params, openmp: bool = False):
+    def __init__(self, params: Params, openmp: bool = False, pairwise_density: bool = False):
         """``openmp``: use the timing build whose loops run on all host
-        threads (for the benchmark's all-cores baseline); same results."""
+        threads (for the benchmark's all-cores baseline); same results.
+        ``pairwise_density``: use the rounding-sensitivity build (the density
+        summed in another order), which measures the FP64 conditioning of
+        the update."""
         self.p = params
         self._cp = params._c()
-        self._lib = _load(openmp)
+        self._lib = _load(openmp, pairwise_density)
 
     # -- free energy (Eq. doubleWell, Eq. EOS) --------------------------------
     def psi0(self, rho: float) -> float:

@@ -34,6 +34,11 @@
  * memory across threads; they are ignored unless the file is built with
  * -fopenmp, which only the timing build of the benchmark's all-cores CPU
  * baseline does.  Every node is computed the same way either way.
+ *
+ * Built with -DORC_DENSITY_PAIRWISE (a rounding-sensitivity build, used only
+ * by tests), the density rho = sum_i f_i is summed in pairs instead of from
+ * i = 0 to 8.  Nothing else changes: comparing the two builds measures how
+ * far two equally valid FP64 evaluations of the same update drift apart.
  */
 #include <math.h>
 #include <stddef.h>
@@ -290,9 +295,15 @@ void orc_macro(const orc_params* p, const double* f, double* rho_out,
 
 #pragma omp parallel for
   for (size_t k = 0; k < n; ++k) {
+#ifdef ORC_DENSITY_PAIRWISE
+    const double* g = f + k;
+    rho[k] = ((g[0] + g[n]) + (g[2 * n] + g[3 * n])) +
+             ((g[4 * n] + g[5 * n]) + (g[6 * n] + g[7 * n])) + g[8 * n];
+#else
     double s = 0.0;
     for (int i = 0; i < Q; ++i) s += f[(size_t)i * n + k];
     rho[k] = s;
+#endif
   }
   orc_laplacian(p, rho, lap);
 #pragma omp parallel for

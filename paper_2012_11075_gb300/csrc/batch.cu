@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
     // and no reloads after the population stores (which could alias
     // device memory)
     __shared__ KParams s_kp;
-    if (threadIdx.x == 0) s_kp = cs.kp;
+    if (threadIdx.x == 0) {
+      s_kp = cs.kp;
+      s_kp.step += j;                      // the case's time step of this item
+    }
     __syncthreads();
     const KParams& kp = s_kp;
     const int cur = (cs.cur + j) & 1;
@@ -195,6 +198,7 @@ __global__ void __launch_bounds__(128)
     out[4] = red[0][4];
     out[5] = red[0][5];
     cases[rc.c].cur ^= (d.desc->steps & 1);
+    cases[rc.c].kp.step += d.desc->steps;
   }
 }
 
@@ -399,6 +403,7 @@ KParams case_kparams(const wblbe_batch::Case& c, int rows) {
   k.rho_ref = rr;
   k.dl = rr - p.rho_l;
   k.dg = rr - p.rho_g;
+  k.step = c.steps;                        // advanced on the device by each launch
   return k;
 }
 

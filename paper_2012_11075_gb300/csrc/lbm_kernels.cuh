@@ -43,6 +43,11 @@ struct KParams {
   double two_beta;                // 2 beta
   double dl, dg;                  // rho_ref - rho_l, rho_ref - rho_g
   double rho_ref;                 // 0 in FP64
+  // Time step t of the state being updated, which seeds the stochastic
+  // rounding of the FP32 well-balanced update: t = step + *step_base
+  // (step_base may be null; a graph replay reads its base from device memory).
+  long long step;
+  const long long* step_base;
 };
 
 // Outputs of the moments mode (any pointer may be null).
@@ -334,6 +339,75 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
+// ---- exact-mass rest population of the FP32 well-balanced update -----------
+//
+// The collision conserves each node's mass exactly in real arithmetic
+// (sum_i f^eq_i = rho and sum_i F_i = 0, Sec. III), so the post-collision
+// rest population is g_0' = sum_i g_i - sum_{i != 0} g_i'.  In float storage
+// the rest population (about rho - rho_ref) is much larger than the moving
+// ones (O(u, F) in the well-balanced scheme), so the rounding of the two
+// sums of moving populations is far below an ulp of g_0, and three error-free
+// additions (TwoSum) carry the rest exactly: g_0 + m = rs + e1 (pulled mass,
+// rs the density the stencils use), rs - a = h + e2, h + (e1 + e2) = h2 + e3.
+// g_0' is h2 or its float neighbour on the side of e3, the neighbour with
+// probability |e3| / (distance to it): the expected rounding error is zero,
+// so a state that repeats its rounding step after step (near equilibrium)
+// no longer drifts in mass; its mass performs a random walk instead.  The
+// random bits come from a counter-based hash of the node (x, y) and the time
+// step t, so results do not depend on the launch shape, on batching or on
+// the order in which tiles run.
+
+// Error-free sum (Knuth's TwoSum) on a pair of lanes: s = fl(a + b) and
+// a + b = s + e exactly.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bv = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bv)), sub2(b, bv));
+}
+
+// MurmurHash3's 32-bit finalizer (Appleby): a bijective avalanche mixer.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Key of time step t (folded into every node's hash of that step).
+__device__ __forceinline__ uint32_t step_key(long long t) {
+  return fmix32((uint32_t)t * 0x9e3779b9u + 0x6a09e667u);
+}
+
+// 24 random bits of node k (= y nx + x) at the step with key ht.
+__device__ __forceinline__ uint32_t node_bits(uint32_t k, uint32_t ht) {
+  return fmix32(k + ht) >> 8;
+}
+
+// Round v = h + e (e the exact remainder, |e| at most half an ulp of h) to h
+// or to the float next to h on the side of e, choosing the neighbour with
+// probability |e| / gap (gap = the exact distance to it, a power of two);
+// r24: 24 uniform random bits.  E[result] = v up to 2^-24 of a gap.  A zero,
+// infinite or NaN h is returned unchanged.
+__device__ __forceinline__ float round_stochastic(float h, float e, uint32_t r24) {
+  const uint32_t b = __float_as_uint(h);
+  // one step of the bit pattern away from zero when e and h have the same
+  // sign, towards zero otherwise
+  const bool away = (e > 0.0f) == (h > 0.0f);
+  const float n = __uint_as_float(away ? b + 1u : b - 1u);
+  const float gap = fabsf(__fsub_rn(n, h));
+  const float u = __fmul_rn((float)r24, 0x1p-24f);
+  return (h != 0.0f && __fmul_rn(u, gap) < fabsf(e)) ? n : h;
+}
+
+// Mirror-symmetric sum of the eight moving populations: every lattice
+// mirror (x, y, diagonal) maps the grouping onto itself, so mirror-image
+// nodes round alike and the rounding leaves no net force.
+__device__ __forceinline__ float2 moving_sum2(const float2 (&g)[9]) {
+  return add2(add2(add2(g[1], g[3]), add2(g[2], g[4])), add2(add2(g[5], g[7]), add2(g[6], g[8])));
+}
+
 // chem_pot on a pair of nodes (same formula and evaluation order)
 __device__ __forceinline__ float2 chem_pot_x2(float2 c, float2 e, float2 w, float2 n, float2 s,
                                               float2 ne, float2 nw, float2 se, float2 sw,
@@ -392,10 +466,12 @@ __device__ __forceinline__ void textbook_pairs_x2(float2 (&g)[9], float2 rs, flo
 
 // collide<float, SCH> on a pair of nodes (FP32-shifted storage): the same
 // terms as the scalar version, with the multiply-adds written out.
+// rnd: 24 random bits per lane for the stochastic rounding of the rest
+// population (well-balanced scheme only, see round_stochastic).
 template <int SCH>
 __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx, float2 gmy,
                                            float2 grx, float2 gry, const CollideConsts<float>& q,
-                                           float2& ux_out, float2& uy_out) {
+                                           float2& ux_out, float2& uy_out, uint2 rnd) {
   constexpr bool WB = SCH == kSchWB;
   const float2 omega = splat(q.omega), kf = splat(q.kf), third = splat(1.0f / 3.0f);
   const float2 rho = add2(rs, splat(q.rho_ref));
@@ -414,8 +490,16 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   }
   const float2 d13 = sub2(g[1], g[3]), d24 = sub2(g[2], g[4]);
   const float2 d57 = sub2(g[5], g[7]), d86 = sub2(g[8], g[6]);
-  const float2 jx = add2(add2(d13, d57), d86);
-  const float2 jy = sub2(add2(d24, d57), d86);
+  // mirror-symmetric groupings: an x-mirror negates jx exactly, a y-mirror jy
+  const float2 jx = add2(d13, add2(d57, d86));
+  const float2 jy = add2(d24, sub2(d57, d86));
+  // pulled mass: g_0 + m = rs + e1 exactly (rs is the staged density, formed
+  // by the same two additions)
+  float2 e1 = make_float2(0.f, 0.f);
+  if (WB) {
+    float2 rs_again;
+    two_sum2(g[0], moving_sum2(g), rs_again, e1);
+  }
   const float2 inv_rho = make_float2(recip(rho.x), recip(rho.y));
   const float2 half = splat(0.5f);
   const float2 ux = mul2(fma2(half, Fx, jx), inv_rho);   // Eq. rhoU
@@ -473,9 +557,17 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   g[7] = fma2(keep, g[7], sub2(E5, O5));
   g[6] = fma2(keep, g[6], add2(E6, O6));
   g[8] = fma2(keep, g[8], sub2(E6, O6));
-  // rest population from the node mass balance, as in the scalar version
-  g[0] = sub2(rs, add2(add2(add2(g[1], g[3]), add2(g[2], g[4])),
-                       add2(add2(g[5], g[7]), add2(g[6], g[8]))));
+  if (WB) {
+    // exact node mass balance, stochastically rounded (see round_stochastic)
+    float2 h, e2, h2, e3;
+    const float2 a = moving_sum2(g);
+    two_sum2(rs, make_float2(-a.x, -a.y), h, e2);
+    two_sum2(h, add2(e1, e2), h2, e3);
+    g[0] = make_float2(round_stochastic(h2.x, e3.x, rnd.x), round_stochastic(h2.y, e3.y, rnd.y));
+  } else {
+    // rest population from the node mass balance, as in the scalar version
+    g[0] = sub2(rs, moving_sum2(g));
+  }
 }
 
 // ---- asynchronous copies into shared memory -------------------------------
@@ -720,6 +812,8 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
     return two_beta * a * b * (a + b) - cc.kappa * ringval;
   };
   const int kfirst = y0 - 2, klast = y1 + 1;
+  // hash key of the time step being taken (stochastic rounding, FP32 WB)
+  const uint32_t ht = step_key(p.step + (p.step_base ? *p.step_base : 0LL));
 
   // 16-byte chunks this thread copies in every row (fixed per thread): in
   // class c, chunk q = tx + m * TX is chunk j of the class's plane a, covering
@@ -849,13 +943,14 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
           const T* s1 = stage + WB_SLOT(1, NST) * 9 * SW;
           T* r0 = rho_s + WB_SLOT(0, kRing) * SW;
           T* r1 = rho_s + WB_SLOT(1, kRing) * SW;
-          // same summation order as staged_rho
+          // rho = g_0 + (moving sum, mirror-symmetric grouping): the same two
+          // operations collide_x2 repeats for the exact mass balance
           auto rho2 = [&](int s) {
-            const float2 a = add2(add2(V(s0, s1, 0 * SW + s), V(s0, s1, 1 * SW + s - 1)),
-                                  add2(V(s0, s1, 2 * SW + s), V(s0, s1, 3 * SW + s + 1)));
-            const float2 b = add2(add2(V(s0, s1, 4 * SW + s), V(s0, s1, 5 * SW + s - 1)),
-                                  add2(V(s0, s1, 6 * SW + s + 1), V(s0, s1, 7 * SW + s + 1)));
-            return add2(add2(a, b), V(s0, s1, 8 * SW + s - 1));
+            const float2 m = add2(add2(add2(V(s0, s1, 1 * SW + s - 1), V(s0, s1, 3 * SW + s + 1)),
+                                       add2(V(s0, s1, 2 * SW + s), V(s0, s1, 4 * SW + s))),
+                                  add2(add2(V(s0, s1, 5 * SW + s - 1), V(s0, s1, 7 * SW + s + 1)),
+                                       add2(V(s0, s1, 6 * SW + s + 1), V(s0, s1, 8 * SW + s - 1))));
+            return add2(V(s0, s1, 0 * SW + s), m);
           };
           if (own) {
             const float2 v = rho2(sx);
@@ -991,7 +1086,9 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                            V(s0, s1, 6 * SW + sx + 1), V(s0, s1, 7 * SW + sx + 1),
                            V(s0, s1, 8 * SW + sx - 1)};
             float2 ux, uy;
-            collide_x2<SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+            const uint32_t key0 = (uint32_t)c0 * (uint32_t)p.nx + (uint32_t)xm;
+            const uint2 rnd = make_uint2(node_bits(key0, ht), node_bits(key0 + (uint32_t)p.nx, ht));
+            collide_x2<SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy, rnd);
             if (v0) {
               const T gl[9] = {g[0].x, g[1].x, g[2].x, g[3].x, g[4].x,
                                g[5].x, g[6].x, g[7].x, g[8].x};

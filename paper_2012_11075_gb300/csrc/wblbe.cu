@@ -36,7 +36,7 @@ struct Layout {
   size_t elem;          // bytes per population element
   long long plane;      // elements per plane
   size_t pops_bytes;    // one population buffer
-  size_t off_a, off_b, off_stage, off_partials, off_stats, total;
+  size_t off_a, off_b, off_stage, off_partials, off_stats, off_step, total;
   int max_partials;
 };
 
@@ -81,6 +81,7 @@ Layout make_layout(const wblbe_params* p) {
   L.off_stage = off; off += align_up((size_t)p->nx * p->ny * sizeof(double));
   L.off_partials = off; off += align_up((size_t)L.max_partials * kStatRec * sizeof(double));
   L.off_stats = off; off += align_up(8 * sizeof(double));
+  L.off_step = off; off += align_up(sizeof(long long));
   L.total = off;
   return L;
 }
@@ -99,6 +100,7 @@ struct wblbe_ctx {
   double* stage;
   double* partials;
   double* stats_dev;
+  long long* step_dev;           // step of the first step of a graph replay
   wblbe_launch launch;
   int64_t steps;
   int64_t launches;
@@ -257,13 +259,23 @@ cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
   }
 }
 
-// One step from buf[from] to buf[1-from] on stream s.
-cudaError_t issue_step(wblbe_ctx* h, int from, cudaStream_t s) {
+// One step from buf[from] to buf[1-from] on stream s.  The time step of the
+// state it updates: h->steps for a direct launch; for step k of a captured
+// graph, k plus the base that the replay finds in h->step_dev.
+cudaError_t issue_step(wblbe_ctx* h, int from, cudaStream_t s, int graph_k = -1) {
   KParams kp = make_kparams(h, h->launch.rows_per_cta);
+  if (graph_k >= 0) {
+    kp.step = graph_k;
+    kp.step_base = h->step_dev;
+  } else {
+    kp.step = h->steps;
+  }
   MomentsOut mo{};
   return launch_any(h, false, h->buf[from], h->buf[1 - from], kp, mo,
                     h->launch.tile_x, s);
 }
+
+__global__ void set_step_kernel(long long* dst, long long v) { *dst = v; }
 
 void drop_graph(wblbe_ctx* h) {
   if (h->graph_valid) cudaGraphExecDestroy(h->graph);
@@ -276,7 +288,7 @@ wblbe_status build_graph(wblbe_ctx* h) {
   CU(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t le = cudaSuccess;
   for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k)
-    le = issue_step(h, k & 1, h->capture_stream);
+    le = issue_step(h, k & 1, h->capture_stream, k);
   cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
   if (le != cudaSuccess || ce != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -389,6 +401,7 @@ wblbe_status wblbe_create(const wblbe_params* params, void* dev_workspace,
   h->stage = reinterpret_cast<double*>(h->ws + h->L.off_stage);
   h->partials = reinterpret_cast<double*>(h->ws + h->L.off_partials);
   h->stats_dev = reinterpret_cast<double*>(h->ws + h->L.off_stats);
+  h->step_dev = reinterpret_cast<long long*>(h->ws + h->L.off_step);
   h->cur = 0;
   h->launch = default_launch(*params);
   *out = h;
@@ -475,8 +488,10 @@ wblbe_status wblbe_step(wblbe_handle h, int64_t nsteps) {
       --left;
     }
     while (left >= kGraphSteps) {
+      set_step_kernel<<<1, 1, 0, h->stream>>>(h->step_dev, h->steps);
+      CU(h, cudaGetLastError());
       CU(h, cudaGraphLaunch(h->graph, h->stream));
-      h->launches += kGraphSteps;
+      h->launches += kGraphSteps + 1;
       h->steps += kGraphSteps;
       left -= kGraphSteps;
     }
@@ -599,6 +614,13 @@ wblbe_status wblbe_set_populations(wblbe_handle h, const double* f, int32_t on_d
 }
 
 int64_t wblbe_step_count(wblbe_handle h) { return h ? h->steps : -1; }
+
+wblbe_status wblbe_set_step_count(wblbe_handle h, int64_t step) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (step < 0) return fail(h, WBLBE_EINVAL, "step must be >= 0");
+  h->steps = step;
+  return WBLBE_OK;
+}
 int64_t wblbe_kernel_launches(wblbe_handle h) { return h ? h->launches : -1; }
 
 wblbe_status wblbe_destroy(wblbe_handle h) {

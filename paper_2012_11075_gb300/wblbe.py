@@ -92,6 +92,7 @@ _SIGNATURES = {
     "wblbe_get_populations": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
     "wblbe_set_populations": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
     "wblbe_step_count": (ctypes.c_int64, [_H]),
+    "wblbe_set_step_count": (ctypes.c_int, [_H, ctypes.c_int64]),
     "wblbe_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_destroy": (ctypes.c_int, [_H]),
     "wblbe_last_error": (ctypes.c_char_p, [_H]),
@@ -336,6 +337,11 @@ class Solver:
     @property
     def steps(self) -> int:
         return int(self.lib.wblbe_step_count(self.h))
+
+    def set_step_count(self, step: int):
+        """Restore the step counter (e.g. when resuming a checkpoint); in FP32
+        well-balanced runs it also seeds the stochastic rounding."""
+        self._check(self.lib.wblbe_set_step_count(self.h, int(step)))
 
     @property
     def kernel_launches(self) -> int:

@@ -7,7 +7,11 @@ Tolerances:
     moving populations are O(u, F), far below the rest population, so the
     global norm alone would not see an error confined to them).  The two
     sides differ only in rounding (fused multiply-adds and summation order on
-    the GPU), which stays at round-off level in these stable runs.
+    the GPU), which stays at round-off level in these stable runs.  Where a
+    well-balanced moving population is so small that its own FP64 round-off
+    exceeds 1e-12 of it, the bar is 4 times the spread between the oracle
+    and the oracle built to sum the density in another order (see
+    tests/gpu_helpers.py); measured, the GPU sits at 1.0-1.4 times it.
   * FP32-shifted storage: float32 has a unit round-off of 6e-8; an O(1)
     population accumulates O(steps * 6e-8 * |g|) of rounding in a
     non-chaotic run, so after 1000 steps we allow 2e-5 of the largest
@@ -25,7 +29,7 @@ import pytest
 from oracle.oracle import STANDARD, WELL_BALANCED
 from paper_2012_11075_gb300 import wblbe
 from paper_2012_11075_gb300 import workloads as wl
-from tests.gpu_helpers import need_gpu, pop_error, run_gpu, run_oracle
+from tests.gpu_helpers import check_per_direction, need_gpu, pop_error, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +51,8 @@ def _check_fp64(pr, scheme, steps, rho0=0.0, launch=None, rho=None):
     glob, per = pop_error(fg, fo)
     assert np.all(np.isfinite(fg))
     assert glob < FP64_TOL, (glob, per)
-    assert per < FP64_TOL, (glob, per)
+    check_per_direction(fg, fo, lambda: run_oracle(pr, scheme, steps, rho0=rho0, rho=rho,
+                                                   pairwise_density=True)[0])
     for k in ("rho", "ux", "uy"):
         scale = max(np.max(np.abs(mo[k])), 1e-300)
         assert np.max(np.abs(mg[k] - mo[k])) <= max(FP64_TOL * scale, 1e-15), k
@@ -382,6 +387,7 @@ def test_checkpoint_resume_is_exact(precision):
     a.close()
     b = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
     b.set_populations(saved)
+    b.set_step_count(50)             # FP32: continues the rounding sequence
     b.step(70)
     got = b.get_populations()
     b.close()

@@ -40,9 +40,12 @@ def _noalloc(lib, params, f_dev, torch):
 
 
 def _compare(ref, ref_st, got, st, pr):
+    # u = (j + F/2) / rho with j a sum of populations of order 1/9 in another
+    # order than the handle's kernel: an absolute floor of 1e-15 covers that
+    # round-off where the velocity itself is tiny (as the other FP64 tests)
     for k in ("rho", "ux", "uy"):
         scale = np.max(np.abs(ref[k]))
-        assert np.max(np.abs(got[k] - ref[k])) <= TOL * max(scale, 1e-300), k
+        assert np.max(np.abs(got[k] - ref[k])) <= max(TOL * scale, 1e-15), k
     mu_scale = 2 * pr.beta * (pr.rho_l - pr.rho_g) ** 3
     assert np.max(np.abs(got["mu"] - ref["mu"])) <= TOL * mu_scale
     assert st["mass"] == pytest.approx(ref_st["mass"], rel=1e-13)
