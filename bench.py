@@ -371,6 +371,9 @@ def run_batched(args, stream, torch):
     for cid in ids:
         states[str(infos[cid]["state"])] = states.get(str(infos[cid]["state"]), 0) + 1
     lat = np.array([done_at.get(cid, t_solve) for cid in ids])
+    by_state = {}
+    for cid, l in zip(ids, lat):
+        by_state.setdefault(str(infos[cid]["state"]), []).append(l)
     launches = b.kernel_launches - l0
     b.close()
     return {"workload": f"batched_{len(specs)}_uneven_cases_wb_fp32",
@@ -384,6 +387,11 @@ def run_batched(args, stream, torch):
             / (measured_peaks().get("hbm_gbs") or 6800.0),
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
+            # every case runs to its step budget unless it goes unstable (the
+            # mix draws tau below the WB stability limit): latency per outcome
+            "latency_by_state": {k: {"count": len(v), "p50_s": float(np.percentile(v, 50)),
+                                     "p99_s": float(np.percentile(v, 99))}
+                                 for k, v in sorted(by_state.items())},
             "states": states, "state_names": {"1": "converged", "2": "budget", "3": "unstable"},
             "gpu_launches": int(launches)}
 
@@ -392,8 +400,12 @@ def run_serving(args, stream, torch, cfg):
     """Continuous batching of relax-to-equilibrium requests arriving as a
     Poisson process (sides 32..1024 log-uniform, case parameters as the
     batched mix), each run to max|u| < 1e-6 (FP32) / 1e-10 (FP64) or 200000
-    steps, for a fixed window per arrival rate; requests are admitted as
-    slots and memory free up."""
+    steps; requests are admitted as slots and memory free up.  Each arrival
+    rate runs until serve_requests requests have completed or its window
+    has passed, whichever comes first.  Latency percentiles are reported
+    over all completed requests and per outcome (converged / budget /
+    unstable: the mix draws tau down to 0.55, below the well-balanced
+    scheme's linear stability limit)."""
     from paper_2012_11075_gb300 import serve, wblbe
     out = {}
     for name, prec in (("fp32", wblbe.FP32_SHIFTED), ("fp64", wblbe.FP64)):
@@ -406,13 +418,17 @@ def run_serving(args, stream, torch, cfg):
                             tile_x=cfg[0], rows_per_tile=cfg[1], steps_per_launch=cfg[2],
                             stream=stream)
             srv = serve.Server(b)
-            rep = srv.run(reqs, duration=args.serve_window, drain=False)
+            rep = srv.run(reqs, duration=args.serve_window, drain=False,
+                          stop_after=args.serve_requests)
             b.close()
             out[name][str(rate)] = rep.summary()
     return {"workload": "poisson_relax_to_equilibrium_wb", "window_s": args.serve_window,
+            "stop_rule": f"each rate until {args.serve_requests} requests completed or "
+                         f"{args.serve_window} s passed",
             "policy": "admit by slot and arena room, one launch per loop, stop at launch "
-                      "boundaries, fixed window (requests still queued or running at the "
-                      "end are reported, not counted as completed)",
+                      "boundaries (requests still queued or running at the end are "
+                      "reported, not counted as completed)",
+            "outcomes": {"1": "converged", "2": "budget", "3": "unstable"},
             "results": out}
 
 
@@ -610,7 +626,8 @@ def main():
     ap.add_argument("--no-ratio50", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
-    ap.add_argument("--serve-window", type=float, default=5.0)
+    ap.add_argument("--serve-window", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50.0, 200.0, 1000.0])
     ap.add_argument("--serve-arena-gb", type=int, default=24)
     args = ap.parse_args()

@@ -442,8 +442,11 @@ void case_tiles(const wblbe_batch::Case& c, int case_idx, const wblbe_batch_conf
                 std::vector<TileDev>& out) {
   const int nx = c.p.nx, ny = c.p.ny;
   const int nseg = std::max(1, ny / std::max(cfg.rows_per_tile, 4));
+  // run boundaries on even rows (the FP32 stochastic rounding draws one hash
+  // per pair of rows 2j, 2j + 1; see pair_uniforms)
+  auto bound = [&](int s) { return s >= nseg ? ny : (int)((long long)s * ny / nseg) & ~1; };
   for (int s = 0; s < nseg; ++s) {
-    const int y0 = (int)((long long)s * ny / nseg), y1 = (int)((long long)(s + 1) * ny / nseg);
+    const int y0 = bound(s), y1 = bound(s + 1);
     for (int x0 = 0; x0 < nx; x0 += cfg.tile_x) {
       TileDev t{};
       t.c = case_idx;

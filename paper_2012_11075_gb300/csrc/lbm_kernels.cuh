@@ -343,19 +343,18 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 //
 // The collision conserves each node's mass exactly in real arithmetic
 // (sum_i f^eq_i = rho and sum_i F_i = 0, Sec. III), so the post-collision
-// rest population is g_0' = sum_i g_i - sum_{i != 0} g_i'.  In float storage
-// the rest population (about rho - rho_ref) is much larger than the moving
-// ones (O(u, F) in the well-balanced scheme), so the rounding of the two
-// sums of moving populations is far below an ulp of g_0, and three error-free
-// additions (TwoSum) carry the rest exactly: g_0 + m = rs + e1 (pulled mass,
-// rs the density the stencils use), rs - a = h + e2, h + (e1 + e2) = h2 + e3.
-// g_0' is h2 or its float neighbour on the side of e3, the neighbour with
-// probability |e3| / (distance to it): the expected rounding error is zero,
-// so a state that repeats its rounding step after step (near equilibrium)
-// no longer drifts in mass; its mass performs a random walk instead.  The
-// random bits come from a counter-based hash of the node (x, y) and the time
-// step t, so results do not depend on the launch shape, on batching or on
-// the order in which tiles run.
+// rest population is g_0' = g_0 + (m - a), m and a the sums of the pulled
+// and of the post-collision moving populations.  In float storage the rest
+// population (about rho - rho_ref) is much larger than the moving ones
+// (O(u, F) in the well-balanced scheme), so the rounding of m, a and m - a is
+// far below an ulp of g_0, and one error-free addition (TwoSum) gives
+// g_0 + (m - a) = h + e exactly.  g_0' is h or its float neighbour on the
+// side of e, the neighbour with probability |e| / (distance to it): the
+// expected rounding error is zero, so a state that repeats its rounding step
+// after step (near equilibrium) no longer drifts in mass; its mass performs
+// a random walk instead.  The random bits come from a counter-based hash of
+// the node (x, y) and the time step t, so results do not depend on the
+// launch shape, on batching or on the order in which tiles run.
 
 // Error-free sum (Knuth's TwoSum) on a pair of lanes: s = fl(a + b) and
 // a + b = s + e exactly.
@@ -380,24 +379,31 @@ __device__ __forceinline__ uint32_t step_key(long long t) {
   return fmix32((uint32_t)t * 0x9e3779b9u + 0x6a09e667u);
 }
 
-// 24 random bits of node k (= y nx + x) at the step with key ht.
-__device__ __forceinline__ uint32_t node_bits(uint32_t k, uint32_t ht) {
-  return fmix32(k + ht) >> 8;
+// Uniform draws in [0, 1) on a 2^-23 grid for the two nodes of column x in
+// rows 2j and 2j + 1 (k = 2j nx + x is the lower node's key): one hash of k
+// and the step key ht; the upper node's draw takes the top bits of the hash
+// times an odd constant, which every bit of the hash feeds.  The pairing is
+// by absolute row, so a node's draw does not depend on the launch shape.
+__device__ __forceinline__ float2 pair_uniforms(uint32_t k, uint32_t ht) {
+  const uint32_t h = fmix32(k + ht);
+  const uint32_t h2 = h * 0x9e3779b9u;
+  // 1.m - 1 with the 23 random bits as the mantissa m: exact
+  return make_float2(__fsub_rn(__uint_as_float(0x3f800000u | (h >> 9)), 1.0f),
+                     __fsub_rn(__uint_as_float(0x3f800000u | (h2 >> 9)), 1.0f));
 }
 
 // Round v = h + e (e the exact remainder, |e| at most half an ulp of h) to h
 // or to the float next to h on the side of e, choosing the neighbour with
 // probability |e| / gap (gap = the exact distance to it, a power of two);
-// r24: 24 uniform random bits.  E[result] = v up to 2^-24 of a gap.  A zero,
-// infinite or NaN h is returned unchanged.
-__device__ __forceinline__ float round_stochastic(float h, float e, uint32_t r24) {
+// u uniform in [0, 1) on a 2^-23 grid.  E[result] = v up to 2^-23 of a gap.
+// A zero, infinite or NaN h is returned unchanged.
+__device__ __forceinline__ float round_stochastic(float h, float e, float u) {
   const uint32_t b = __float_as_uint(h);
   // one step of the bit pattern away from zero when e and h have the same
   // sign, towards zero otherwise
   const bool away = (e > 0.0f) == (h > 0.0f);
   const float n = __uint_as_float(away ? b + 1u : b - 1u);
   const float gap = fabsf(__fsub_rn(n, h));
-  const float u = __fmul_rn((float)r24, 0x1p-24f);
   return (h != 0.0f && __fmul_rn(u, gap) < fabsf(e)) ? n : h;
 }
 
@@ -466,12 +472,12 @@ __device__ __forceinline__ void textbook_pairs_x2(float2 (&g)[9], float2 rs, flo
 
 // collide<float, SCH> on a pair of nodes (FP32-shifted storage): the same
 // terms as the scalar version, with the multiply-adds written out.
-// rnd: 24 random bits per lane for the stochastic rounding of the rest
+// rnd: a uniform draw per lane for the stochastic rounding of the rest
 // population (well-balanced scheme only, see round_stochastic).
 template <int SCH>
 __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx, float2 gmy,
                                            float2 grx, float2 gry, const CollideConsts<float>& q,
-                                           float2& ux_out, float2& uy_out, uint2 rnd) {
+                                           float2& ux_out, float2& uy_out, float2 rnd) {
   constexpr bool WB = SCH == kSchWB;
   const float2 omega = splat(q.omega), kf = splat(q.kf), third = splat(1.0f / 3.0f);
   const float2 rho = add2(rs, splat(q.rho_ref));
@@ -493,13 +499,8 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   // mirror-symmetric groupings: an x-mirror negates jx exactly, a y-mirror jy
   const float2 jx = add2(d13, add2(d57, d86));
   const float2 jy = add2(d24, sub2(d57, d86));
-  // pulled mass: g_0 + m = rs + e1 exactly (rs is the staged density, formed
-  // by the same two additions)
-  float2 e1 = make_float2(0.f, 0.f);
-  if (WB) {
-    float2 rs_again;
-    two_sum2(g[0], moving_sum2(g), rs_again, e1);
-  }
+  // pulled moving populations' sum (rs is g_0 plus this, formed in staging)
+  const float2 m_in = WB ? moving_sum2(g) : make_float2(0.f, 0.f);
   const float2 inv_rho = make_float2(recip(rho.x), recip(rho.y));
   const float2 half = splat(0.5f);
   const float2 ux = mul2(fma2(half, Fx, jx), inv_rho);   // Eq. rhoU
@@ -558,12 +559,10 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   g[6] = fma2(keep, g[6], add2(E6, O6));
   g[8] = fma2(keep, g[8], sub2(E6, O6));
   if (WB) {
-    // exact node mass balance, stochastically rounded (see round_stochastic)
-    float2 h, e2, h2, e3;
-    const float2 a = moving_sum2(g);
-    two_sum2(rs, make_float2(-a.x, -a.y), h, e2);
-    two_sum2(h, add2(e1, e2), h2, e3);
-    g[0] = make_float2(round_stochastic(h2.x, e3.x, rnd.x), round_stochastic(h2.y, e3.y, rnd.y));
+    // exact node mass balance g_0 + (m - a), stochastically rounded
+    float2 h, e;
+    two_sum2(g[0], sub2(m_in, moving_sum2(g)), h, e);
+    g[0] = make_float2(round_stochastic(h.x, e.x, rnd.x), round_stochastic(h.y, e.y, rnd.y));
   } else {
     // rest population from the node mass balance, as in the scalar version
     g[0] = sub2(rs, moving_sum2(g));
@@ -1086,8 +1085,16 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                            V(s0, s1, 6 * SW + sx + 1), V(s0, s1, 7 * SW + sx + 1),
                            V(s0, s1, 8 * SW + sx - 1)};
             float2 ux, uy;
-            const uint32_t key0 = (uint32_t)c0 * (uint32_t)p.nx + (uint32_t)xm;
-            const uint2 rnd = make_uint2(node_bits(key0, ht), node_bits(key0 + (uint32_t)p.nx, ht));
+            // draws of rows c0 and c0 + 1 (one hash when c0 is even, the
+            // usual case; the parity of c0 is fixed within a CTA)
+            const uint32_t kx = (uint32_t)c0 * (uint32_t)p.nx + (uint32_t)xm;
+            float2 rnd;
+            if ((c0 & 1) == 0) {
+              rnd = pair_uniforms(kx, ht);
+            } else {
+              rnd = make_float2(pair_uniforms(kx - (uint32_t)p.nx, ht).y,
+                                pair_uniforms(kx + (uint32_t)p.nx, ht).x);
+            }
             collide_x2<SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy, rnd);
             if (v0) {
               const T gl[9] = {g[0].x, g[1].x, g[2].x, g[3].x, g[4].x,
@@ -1184,8 +1191,10 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 }
 
 // One CTA per strip segment: blockIdx.x picks the strip, blockIdx.y the run
-// of p.rows rows.  Moments mode writes the per-CTA stats record.
-template <typename T, int SCH, bool MOMENTS, int TX>
+// of p.rows rows.  MODE is a StripMode: the moments mode, and the step with
+// statistics (a step that also reduces the stats of the state it starts
+// from), write the per-CTA stats record.
+template <typename T, int SCH, int MODE, int TX>
 __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
     lbm_strip_kernel(const T* __restrict__ src, T* __restrict__ dst,
                      const KParams p, const MomentsOut mo) {
@@ -1193,11 +1202,10 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
   const int x0 = blockIdx.x * TX;
   const int y0 = blockIdx.y * p.rows;
   const int y1 = min(y0 + p.rows, p.ny);
-  double* rec = (MOMENTS && mo.partials)
+  double* rec = (MODE != kModeStep && mo.partials)
                     ? mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec
                     : nullptr;
-  strip_pass<T, SCH, MOMENTS ? kModeMoments : kModeStep, TX>(src, dst, p, mo, x0, y0, y1, rec,
-                                                              smem_raw);
+  strip_pass<T, SCH, MODE, TX>(src, dst, p, mo, x0, y0, y1, rec, smem_raw);
 }
 
 // Final reduction of the per-CTA records, one block, fixed order.

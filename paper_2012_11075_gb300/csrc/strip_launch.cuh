@@ -17,13 +17,13 @@ inline size_t strip_smem(int tile) {
 }
 
 // Allow every instantiation the dynamic shared memory it launches with.
-template <typename T, int SCH, bool MOM, int TX>
+template <typename T, int SCH, int MODE, int TX>
 cudaError_t allow_smem_tx() {
-  return cudaFuncSetAttribute(lbm_strip_kernel<T, SCH, MOM, TX>,
+  return cudaFuncSetAttribute(lbm_strip_kernel<T, SCH, MODE, TX>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)strip_smem<T>(TX));
 }
-template <typename T, int SCH, bool MOM>
+template <typename T, int SCH, int MOM>
 cudaError_t allow_smem_mom() {
   cudaError_t e = cudaSuccess, r;
   if ((r = allow_smem_tx<T, SCH, MOM, 32>()) != cudaSuccess) e = r;
@@ -35,14 +35,16 @@ cudaError_t allow_smem_mom() {
 template <int SCH>
 cudaError_t allow_smem_scheme() {
   cudaError_t e = cudaSuccess, r;
-  if ((r = allow_smem_mom<double, SCH, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_mom<double, SCH, false>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_mom<float, SCH, true>()) != cudaSuccess) e = r;
-  if ((r = allow_smem_mom<float, SCH, false>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<double, SCH, kModeStep>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<double, SCH, kModeMoments>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<double, SCH, kModeStepStats>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<float, SCH, kModeStep>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<float, SCH, kModeMoments>()) != cudaSuccess) e = r;
+  if ((r = allow_smem_mom<float, SCH, kModeStepStats>()) != cudaSuccess) e = r;
   return e;
 }
 
-template <typename T, int SCH, bool MOM, int TX>
+template <typename T, int SCH, int MOM, int TX>
 cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
                       cudaStream_t s) {
   dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + kp.rows - 1) / kp.rows);
@@ -51,7 +53,7 @@ cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const Momen
   return cudaGetLastError();
 }
 
-template <typename T, int SCH, bool MOM>
+template <typename T, int SCH, int MOM>
 cudaError_t launch_strip(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
                          int tile, cudaStream_t s) {
   switch (tile) {
@@ -63,21 +65,29 @@ cudaError_t launch_strip(const void* src, void* dst, const KParams& kp, const Mo
   }
 }
 
+// mode: a StripMode (step, moments, step with statistics)
+template <typename T, int SCH>
+cudaError_t launch_mode(int mode, const void* src, void* dst, const KParams& kp,
+                        const MomentsOut& mo, int tile, cudaStream_t s) {
+  switch (mode) {
+    case kModeStep: return launch_strip<T, SCH, kModeStep>(src, dst, kp, mo, tile, s);
+    case kModeMoments: return launch_strip<T, SCH, kModeMoments>(src, dst, kp, mo, tile, s);
+    case kModeStepStats: return launch_strip<T, SCH, kModeStepStats>(src, dst, kp, mo, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 template <int SCH>
-cudaError_t launch_scheme(bool fp64, bool moments, const void* src, void* dst,
+cudaError_t launch_scheme(bool fp64, int mode, const void* src, void* dst,
                           const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s) {
-  if (fp64)
-    return moments ? launch_strip<double, SCH, true>(src, dst, kp, mo, tile, s)
-                   : launch_strip<double, SCH, false>(src, dst, kp, mo, tile, s);
-  return moments ? launch_strip<float, SCH, true>(src, dst, kp, mo, tile, s)
-                 : launch_strip<float, SCH, false>(src, dst, kp, mo, tile, s);
+  return fp64 ? launch_mode<double, SCH>(mode, src, dst, kp, mo, tile, s)
+              : launch_mode<float, SCH>(mode, src, dst, kp, mo, tile, s);
 }
 
 // Resident CTAs per SM of the step kernel at this tile width.
 template <typename T, int SCH, int TX>
 int resident_tx() {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_strip_kernel<T, SCH, false, TX>, TX,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lbm_strip_kernel<T, SCH, kModeStep, TX>, TX,
                                                     strip_smem<T>(TX)) != cudaSuccess)
     return 1;
   return n > 0 ? n : 1;
@@ -97,14 +107,14 @@ int resident_scheme(bool fp64, int tile) {
 }
 
 // The comparison variants (scheme codes 2 and 3), defined in strip_variants.cu.
-cudaError_t launch_variant(int sch, bool fp64, bool moments, const void* src, void* dst,
+cudaError_t launch_variant(int sch, bool fp64, int mode, const void* src, void* dst,
                            const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s);
 int resident_variant(int sch, bool fp64, int tile);
 cudaError_t allow_smem_variants();
 // Scheme code 4 (FP64 tile kernel, 32 x 16 nodes per CTA): launch, and the
 // number of per-CTA statistics records its moments pass writes.
 constexpr int kSchE6 = 4;
-cudaError_t launch_e6(bool moments, const void* src, void* dst, const KParams& kp,
+cudaError_t launch_e6(int mode, const void* src, void* dst, const KParams& kp,
                       const MomentsOut& mo, cudaStream_t s);
 int e6_partials(int nx, int ny);
 // Bounds-check counts of the other translation units (bounds-checked build).

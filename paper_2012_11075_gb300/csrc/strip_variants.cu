@@ -39,7 +39,7 @@ __device__ __forceinline__ int e6_wrap(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
-template <bool MOMENTS>
+template <int MODE>
 __global__ void __launch_bounds__(kE6Threads)
     e6_tile_kernel(const double* __restrict__ src, double* __restrict__ dst, const KParams p,
                    const MomentsOut mo) {
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kE6Threads)
   __syncthreads();
   const CollideConsts<double> cc(p);
   StatsAcc acc;
-  const bool acc_on = MOMENTS;
+  const bool acc_on = MODE != kModeStep;
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int lx = tid & 31, ly = (tid >> 5) + 8 * half;
@@ -89,12 +89,12 @@ __global__ void __launch_bounds__(kE6Threads)
       for (int i = 0; i < 9; ++i) g[i] = pulled(i, x, y);
       double ux, uy;
       collide<double, kSchStandard>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
-      emit_node<double, MOMENTS ? kModeMoments : kModeStep, false>(
+      emit_node<double, MODE, false>(
           p, mo, dst, y, x, x, false, false, g, rs, mu_t[(ly + 2) * kMuW + lx + 2], ux, uy,
           acc, acc_on);
     }
   }
-  if (MOMENTS && mo.partials) {
+  if (MODE != kModeStep && mo.partials) {
     double v[kStatRec] = {acc.mass, acc.kin, acc.u2, acc.mumin, acc.mumax, (double)acc.bad};
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -140,24 +140,28 @@ int e6_partials(int nx, int ny) {
   return ((nx + kE6Tx - 1) / kE6Tx) * ((ny + kE6Ty - 1) / kE6Ty);
 }
 
-cudaError_t launch_e6(bool moments, const void* src, void* dst, const KParams& kp,
+cudaError_t launch_e6(int mode, const void* src, void* dst, const KParams& kp,
                       const MomentsOut& mo, cudaStream_t s) {
   dim3 grid((kp.nx + kE6Tx - 1) / kE6Tx, (kp.ny + kE6Ty - 1) / kE6Ty);
-  if (moments)
-    e6_tile_kernel<true><<<grid, kE6Threads, 0, s>>>(static_cast<const double*>(src),
-                                                      static_cast<double*>(dst), kp, mo);
-  else
-    e6_tile_kernel<false><<<grid, kE6Threads, 0, s>>>(static_cast<const double*>(src),
-                                                       static_cast<double*>(dst), kp, mo);
+  const double* in = static_cast<const double*>(src);
+  double* out = static_cast<double*>(dst);
+  switch (mode) {
+    case kModeStep: e6_tile_kernel<kModeStep><<<grid, kE6Threads, 0, s>>>(in, out, kp, mo); break;
+    case kModeMoments: e6_tile_kernel<kModeMoments><<<grid, kE6Threads, 0, s>>>(in, out, kp, mo); break;
+    case kModeStepStats:
+      e6_tile_kernel<kModeStepStats><<<grid, kE6Threads, 0, s>>>(in, out, kp, mo);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_variant(int sch, bool fp64, bool moments, const void* src, void* dst,
+cudaError_t launch_variant(int sch, bool fp64, int mode, const void* src, void* dst,
                            const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s) {
   if (sch == kSchPressure)
-    return launch_scheme<kSchPressure>(fp64, moments, src, dst, kp, mo, tile, s);
+    return launch_scheme<kSchPressure>(fp64, mode, src, dst, kp, mo, tile, s);
   if (sch == kSchTextbook)
-    return launch_scheme<kSchTextbook>(fp64, moments, src, dst, kp, mo, tile, s);
+    return launch_scheme<kSchTextbook>(fp64, mode, src, dst, kp, mo, tile, s);
   return cudaErrorInvalidValue;
 }
 

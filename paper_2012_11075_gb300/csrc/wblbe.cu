@@ -238,25 +238,35 @@ wblbe_launch default_launch(const wblbe_params& p) {
   if (segs < 1) segs = 1;
   long long rows = (p.ny + segs - 1) / segs;
   if (rows < 8) rows = 8;
+  rows += rows & 1;          // even: every CTA starts on an even row (see pair_uniforms)
   if (rows > p.ny) rows = p.ny;
   l.rows_per_cta = (int)rows;
   return l;
 }
 
-cudaError_t launch_any(const wblbe_ctx* h, bool moments, const void* src,
+// mode: kModeStep, kModeMoments or kModeStepStats (see StripMode)
+cudaError_t launch_any(const wblbe_ctx* h, int mode, const void* src,
                        void* dst, const KParams& kp, const MomentsOut& mo,
                        int tile, cudaStream_t s) {
   const bool fp64 = h->p.precision == WBLBE_FP64;
   switch (h->p.scheme) {
     case WBLBE_STANDARD:
-      return launch_scheme<kSchStandard>(fp64, moments, src, dst, kp, mo, tile, s);
+      return launch_scheme<kSchStandard>(fp64, mode, src, dst, kp, mo, tile, s);
     case WBLBE_WELL_BALANCED:
-      return launch_scheme<kSchWB>(fp64, moments, src, dst, kp, mo, tile, s);
+      return launch_scheme<kSchWB>(fp64, mode, src, dst, kp, mo, tile, s);
     case WBLBE_STANDARD_E6:
-      return launch_e6(moments, src, dst, kp, mo, s);
+      return launch_e6(mode, src, dst, kp, mo, s);
     default:
-      return launch_variant(h->p.scheme, fp64, moments, src, dst, kp, mo, tile, s);
+      return launch_variant(h->p.scheme, fp64, mode, src, dst, kp, mo, tile, s);
   }
+}
+
+// Per-CTA statistics records a step launch writes in the step-with-statistics
+// mode (the E6 tile kernel uses fixed 32 x 16 tiles).
+long long step_records(const wblbe_ctx* h) {
+  if (h->p.scheme == WBLBE_STANDARD_E6) return e6_partials(h->p.nx, h->p.ny);
+  const long long tx = h->launch.tile_x, rows = h->launch.rows_per_cta;
+  return ((h->p.nx + tx - 1) / tx) * ((h->p.ny + rows - 1) / rows);
 }
 
 // One step from buf[from] to buf[1-from] on stream s.  The time step of the
@@ -271,7 +281,7 @@ cudaError_t issue_step(wblbe_ctx* h, int from, cudaStream_t s, int graph_k = -1)
     kp.step = h->steps;
   }
   MomentsOut mo{};
-  return launch_any(h, false, h->buf[from], h->buf[1 - from], kp, mo,
+  return launch_any(h, kModeStep, h->buf[from], h->buf[1 - from], kp, mo,
                     h->launch.tile_x, s);
 }
 
@@ -310,7 +320,7 @@ wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,
   const int tile = h->p.nx >= 128 ? 128 : (h->p.nx > 32 ? 64 : 32);
   KParams kp = make_kparams(h, kMomentsRows);
   MomentsOut mo{rho, ux, uy, mu, h->partials};
-  CU(h, launch_any(h, true, h->buf[h->cur], nullptr, kp, mo, tile, h->stream));
+  CU(h, launch_any(h, kModeMoments, h->buf[h->cur], nullptr, kp, mo, tile, h->stream));
   const int n = h->p.scheme == WBLBE_STANDARD_E6
                     ? e6_partials(h->p.nx, h->p.ny)
                     : ((h->p.nx + tile - 1) / tile) * ((h->p.ny + kMomentsRows - 1) / kMomentsRows);
@@ -335,6 +345,31 @@ wblbe_status read_stats(wblbe_ctx* h, wblbe_stats* out) {
     out->mass_drift_rel = h->mass0 != 0.0 ? (v[0] - h->mass0) / h->mass0 : 0.0;
   }
   return WBLBE_OK;
+}
+
+// One step from the current state in the step-with-statistics mode: the
+// kernel reduces the statistics of the state f(t) it starts from (the same
+// rho, u and mu a moments pass computes) while it writes f(t+1) to the other
+// buffer.  The handle keeps f(t) until the caller adopts the step with
+// adopt_stats_step; the statistics land in h->stats_dev.  Needs
+// step_records(h) <= the workspace's record capacity.
+wblbe_status stats_step(wblbe_ctx* h) {
+  KParams kp = make_kparams(h, h->launch.rows_per_cta);
+  kp.step = h->steps;
+  MomentsOut mo{};
+  mo.partials = h->partials;
+  CU(h, launch_any(h, kModeStepStats, h->buf[h->cur], h->buf[1 - h->cur], kp, mo,
+                   h->launch.tile_x, h->stream));
+  stats_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, (int)step_records(h),
+                                                  h->stats_dev);
+  CU(h, cudaGetLastError());
+  h->launches += 2;
+  return WBLBE_OK;
+}
+
+void adopt_stats_step(wblbe_ctx* h) {
+  h->cur ^= 1;
+  h->steps += 1;
 }
 
 wblbe_status reset_mass(wblbe_ctx* h) {
@@ -543,10 +578,22 @@ wblbe_status wblbe_run_until_equilibrium(wblbe_handle h, double umax_tol,
   if (check_every < 1 || max_steps < 0 || !(umax_tol >= 0.0))
     return fail(h, WBLBE_EINVAL, "need check_every >= 1, max_steps >= 0, umax_tol >= 0");
   if (steps_done) *steps_done = 0;
+  if (!h->have_state) return fail(h, WBLBE_EINVAL, "no state: call wblbe_init_rho first");
+  DeviceGuard dg(h->device);
+  // A check reduces the statistics inside the step that leaves the checked
+  // state (no separate pass over the nine planes): that step writes f(t+1)
+  // to the other buffer, and is adopted as the first step of the next chunk
+  // unless the run stops at this check, in which case the state stays f(t).
+  // Lattices whose step grid has more CTAs than the workspace has records
+  // (launch shapes with very few rows per CTA) fall back to a moments pass.
+  const bool fused = step_records(h) <= h->L.max_partials;
   int64_t done = 0;
   wblbe_stats s{};
   for (;;) {
-    wblbe_status st = wblbe_moments(h, nullptr, nullptr, nullptr, nullptr, 1, &s);
+    wblbe_status st = fused ? stats_step(h)
+                            : run_moments(h, nullptr, nullptr, nullptr, nullptr);
+    if (st != WBLBE_OK) return st;
+    st = read_stats(h, &s);
     if (st != WBLBE_OK) return st;
     if (out) *out = s;
     if (steps_done) *steps_done = done;
@@ -554,6 +601,11 @@ wblbe_status wblbe_run_until_equilibrium(wblbe_handle h, double umax_tol,
     if (s.umax < umax_tol) return WBLBE_OK;
     if (done >= max_steps) return fail(h, WBLBE_ENOTCONVERGED, "max|u| = %g after %lld steps", s.umax, (long long)done);
     int64_t n = check_every < max_steps - done ? check_every : max_steps - done;
+    if (fused) {
+      adopt_stats_step(h);
+      done += 1;
+      n -= 1;
+    }
     st = wblbe_step(h, n);
     if (st != WBLBE_OK) return st;
     done += n;

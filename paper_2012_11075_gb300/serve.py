@@ -25,6 +25,9 @@ import numpy as np
 
 
 REJECTED = -2                   # Request.state of a request that can never fit
+# Request.state after completion: the batch's case states
+CONVERGED, BUDGET, UNSTABLE = 1, 2, 3
+OUTCOMES = {CONVERGED: "converged", BUDGET: "budget", UNSTABLE: "unstable"}
 
 
 @dataclass
@@ -54,13 +57,24 @@ class ServeReport:
     node_steps: float = 0.0
     launches: int = 0
 
-    def latencies(self):
-        return np.array([r.finished - r.arrival for r in self.completed])
+    def latencies(self, state=None):
+        """Completion minus arrival of the completed requests (of one outcome
+        state, or all)."""
+        return np.array([r.finished - r.arrival for r in self.completed
+                         if state is None or r.state == state])
 
     def summary(self) -> dict:
+        """Counts, throughput and latency percentiles.  Latency is reported
+        for all completed requests and separately per outcome: converged
+        (max|u| below the tolerance), budget (step budget reached) and
+        unstable (a non-finite value); the converged requests' step counts
+        to the tolerance are given too."""
+        def pct(a, q):
+            return float(np.percentile(a, q)) if len(a) else None
+
         lat = self.latencies()
         states = collections.Counter(r.state for r in self.completed)
-        return {
+        out = {
             "offered": self.offered,
             "admitted": self.admitted,
             "completed": len(self.completed),
@@ -69,12 +83,21 @@ class ServeReport:
             "running_at_end": self.running_at_end,
             "elapsed_s": self.elapsed,
             "completed_per_s": len(self.completed) / self.elapsed if self.elapsed > 0 else 0.0,
-            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
-            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "p50_latency_s": pct(lat, 50),
+            "p99_latency_s": pct(lat, 99),
             "mlups": self.node_steps / self.elapsed / 1e6 if self.elapsed > 0 else 0.0,
             "launches": self.launches,
             "states": {str(k): v for k, v in sorted(states.items())},
         }
+        for state, name in OUTCOMES.items():
+            a = self.latencies(state)
+            out[f"{name}_count"] = int(len(a))
+            out[f"{name}_p50_latency_s"] = pct(a, 50)
+            out[f"{name}_p99_latency_s"] = pct(a, 99)
+        steps = np.array([r.steps for r in self.completed if r.state == CONVERGED])
+        out["converged_p50_steps"] = pct(steps, 50)
+        out["converged_p99_steps"] = pct(steps, 99)
+        return out
 
 
 class Server:
@@ -139,11 +162,14 @@ class Server:
             self.batch.retire(cid)
             self.report.completed.append(req)
 
-    def run(self, requests, duration: float, drain: bool = False):
+    def run(self, requests, duration: float, drain: bool = False, stop_after=None):
         """Serve ``requests`` (sorted by arrival) in real time until
-        ``duration`` seconds (and, with ``drain``, until all finished)."""
+        ``duration`` seconds (and, with ``drain``, until all finished), or
+        until ``stop_after`` requests have completed, whichever comes first."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         while True:
+            if stop_after is not None and len(self.report.completed) >= stop_after:
+                break
             t = self.now()
             while pending and pending[0].arrival <= t:
                 self.submit(pending.popleft())

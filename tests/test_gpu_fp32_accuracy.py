@@ -1,14 +1,20 @@
 """Accuracy of the FP32-shifted storage on the equilibrium quantities of
-Sec. IV, against references that do not come from the CUDA path: the
-discrete equilibrium S = {mu = const, u = 0} of a flat slab solved by
-Newton's method without the LBE, the coexistence densities of the double
-well, and the 2D Young-Laplace jump sigma / R with sigma of Sec. IV.B.
+Sec. IV, against references that do not come from the CUDA path's float32
+arithmetic: the FP64 run of the same case (which the parity tests pin to the
+FP64 oracle), the discrete equilibrium S = {mu = const, u = 0} of a flat
+slab solved by Newton's method without the LBE, and the 2D Young-Laplace
+jump sigma / R with sigma of Sec. IV.B.
 
-Bounds (FP32-shifted, well-balanced scheme): spurious velocity relative to
-the mean flow below 1e-6, bulk densities at the double-well minima within
-2e-4, interface positions within a drift that the rounding bias of a
-near-steady state explains, and the Laplace jump in the same O(W/R) window
-as the FP64 run."""
+The FP32 well-balanced update takes the rest population from the exact node
+mass balance and rounds it stochastically (zero-mean rounding seeded by the
+node and the step), with mirror-symmetric moment sums.  So near a steady
+state the rounding no longer accumulates into a drift: the mass performs a
+random walk of relative size about ulp(g_0) sqrt(steps / nodes) / rho, the
+velocity floor falls to a few 1e-9, and an interface moves only by the
+random walk the rounding noise gives it.  That noise also seeds the
+x-alternating bulk mode of the well-balanced scheme, which grows for
+tau < (2 + sqrt 2)/4 (see test_stability.py): the slab runs here use
+tau >= 0.9, or a single column, where the mode does not exist."""
 import numpy as np
 import pytest
 
@@ -27,62 +33,104 @@ def _gpu():
     wblbe.load_library()
 
 
-def _crossings(col, level):
-    """Positions where a periodic profile crosses level (linear interpolation)."""
-    n = col.size
+def _run(pr, precision, steps):
+    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED, precision))
+    s.init_rho(pr.rho)
+    s.step(steps)
+    m, st = s.moments()
+    s.close()
+    assert not st["nonfinite"]
+    return m, st
+
+
+def _centroid_shift(rho_a, rho_b, lo, hi):
+    """Periodic centroid of the liquid fraction of rho_a minus that of rho_b
+    (x, y), from the phases of the first Fourier moments."""
     out = []
-    for j in range(n):
-        a, b = col[j], col[(j + 1) % n]
-        if (a - level) * (b - level) < 0:
-            out.append(j + (level - a) / (b - a))
+    for axis in (1, 0):
+        n = rho_a.shape[axis]
+        ph = np.exp(2j * np.pi * np.arange(n) / n)
+        ph = ph[None, :] if axis == 1 else ph[:, None]
+        za, zb = ((np.clip((r - lo) / (hi - lo), 0.0, 1.0) * ph).sum() for r in (rho_a, rho_b))
+        out.append(np.angle(za / zb) / (2 * np.pi) * n)
     return np.array(out)
 
 
-def test_fp32_flat_slab_against_discrete_equilibrium():
-    """Odd slab 4 x 201 (W = 4, ratio 10, tau = 0.8) from the tanh profile,
-    50000 steps in FP32-shifted storage, against the Newton solution of the
-    discrete balance (vapour band between the two interfaces).  FP32 rounding
-    repeats identically at every step of a near-steady state, so its small
-    biases accumulate: the slab as a whole drifts along y (a mean velocity U
-    of a few 1e-6) and the mass drifts.  Checked: the band width within 5e-3
-    of the Newton solution's and the drift of the band below 0.1 lattice
-    units, the velocity relative to U below 1e-6, |U| below 1e-5, the bulk
-    densities within 2e-4 (liquid) and 2e-5 (vapour) of the double-well
-    minima, and the mass within 1e-4."""
+def _shift(field, dx, dy):
+    """field translated by (dx, dy) lattice units (Fourier interpolation)."""
+    ny, nx = field.shape
+    kx = np.fft.fftfreq(nx)[None, :]
+    ky = np.fft.fftfreq(ny)[:, None]
+    return np.real(np.fft.ifft2(np.fft.fft2(field) * np.exp(-2j * np.pi * (kx * dx + ky * dy))))
+
+
+def test_fp32_flat_slab_against_fp64_and_discrete_equilibrium():
+    """Odd slab 4 x 201 (W = 4, ratio 10, tau = 1.0) from the tanh profile,
+    50000 steps: the FP32 profile within 2e-6 of the FP64 run's, both near
+    the Newton solution of the discrete balance (still relaxing), velocity
+    below 1e-7, the slab's mean velocity below 1e-8, the mass within 1e-6
+    (804 nodes: the random walk of the rounding is largest on small
+    lattices)."""
     pr = wl.flat_interface(nx=4, ny=201)
+    pr.tau = 1.0
     rN, _ = eq.discrete_flat_equilibrium(pr.rho[:, 0], pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
-    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED, wblbe.FP32_SHIFTED))
-    s.init_rho(pr.rho)
-    s.step(50000)
-    m, st = s.moments()
-    s.close()
-    assert not st["nonfinite"] and abs(st["mass_drift_rel"]) < 1e-4
-    r = m["rho"]
-    cN, c32 = _crossings(rN, 0.55), _crossings(r[:, 0], 0.55)
-    assert cN.size == 2 and c32.size == 2
-    assert abs((c32[1] - c32[0]) - (cN[1] - cN[0])) < 5e-3
-    assert np.max(np.abs(c32 - cN)) < 0.1
-    U = (r * m["uy"]).sum() / r.sum()
-    assert abs(U) < 1e-5
-    assert np.max(np.abs(m["uy"] - U)) < 1e-6 and np.max(np.abs(m["ux"])) < 1e-6
-    assert abs(r[0, 0] - pr.rho_l) < 2e-4
-    assert abs(r[100, 0] - pr.rho_g) < 2e-5
+    m32, s32 = _run(pr, wblbe.FP32_SHIFTED, 50000)
+    m64, s64 = _run(pr, wblbe.FP64, 50000)
+    r = m32["rho"]
+    assert abs(s32["mass_drift_rel"]) < 1e-6
+    assert np.max(np.abs(r - m64["rho"])) < 2e-6
+    assert np.max(np.abs(m64["rho"][:, 0] - rN)) < 1e-4 and np.max(np.abs(r[:, 0] - rN)) < 1e-4
+    U = (r * m32["uy"]).sum() / r.sum()
+    assert abs(U) < 1e-8
+    assert s32["umax"] < 1e-7
 
 
-def test_fp32_laplace_jump():
-    """Droplet 256^2, R = 60 (W = 4, ratio 10, tau = 1.0), 100000 steps in
-    FP32-shifted storage: p_0(rho_in) - p_0(rho_out) = sigma / R within 2 %,
-    both bulk densities above saturation, as in the FP64 run."""
-    radius = 60.0
+def test_fp32_thin_slab_reaches_discrete_equilibrium():
+    """Single-column slab 1 x 21 (tau = 0.8; one column has no x-alternating
+    mode), 50000 steps: the FP32 profile within 5e-5 of the Newton solution,
+    mu uniform to 1e-7, velocity below 1e-7.  (Deterministic rounding froze
+    this slab at a mu spread of 1e-5: corrections below half an ulp of g_0
+    were lost.)"""
+    ny = 21
+    y = np.arange(ny, dtype=float)
+    d = np.minimum(y, ny - y)
+    prof = 0.55 + 0.45 * np.tanh(2 * (d - ny / 4) / 4.0)
+    beta = wl.beta_for_width(0.01, 4.0, 1.0, 0.1)
+    pr = wl.Problem(1, ny, 0.8, 0.01, beta, 1.0, 0.1, prof[:, None].copy())
+    rN, _ = eq.discrete_flat_equilibrium(prof, 0.01, beta, 1.0, 0.1)
+    m, st = _run(pr, wblbe.FP32_SHIFTED, 50000)
+    assert np.max(np.abs(m["rho"][:, 0] - rN)) < 5e-5
+    assert st["mu_max"] - st["mu_min"] < 1e-7
+    assert st["umax"] < 1e-7
+
+
+@pytest.mark.parametrize("radius", [40.0, 60.0])
+def test_fp32_droplet_against_fp64_long_run(radius):
+    """Droplet 256^2 (W = 4, ratio 10, tau = 1.0), 100000 steps in both
+    precisions.  FP32 against FP64: mass within 1e-7 (relative), the
+    droplet's centroid within 2e-4 lattice units, the density field within
+    5e-5 and, with the centroid shift removed, within 1e-5; bulk densities
+    within 1e-6, max|u| within 0.1 %, the Laplace jump Delta p R / sigma
+    within 1e-4 of FP64's and within the O(W/R) window of 1."""
     pr = wl.droplet(n=256, radius=radius, tau=1.0)
-    s = wblbe.Solver(gpu_params(pr, WELL_BALANCED, wblbe.FP32_SHIFTED))
-    s.init_rho(pr.rho)
-    s.step(100000)
-    m, st = s.moments()
-    s.close()
-    assert not st["nonfinite"] and abs(st["mass_drift_rel"]) < 1e-4
-    rin, rout = m["rho"][128, 128], m["rho"][0, 0]
+    m32, s32 = _run(pr, wblbe.FP32_SHIFTED, 100000)
+    m64, s64 = _run(pr, wblbe.FP64, 100000)
+    assert abs(s32["mass_drift_rel"]) < 1e-7
+    shift = _centroid_shift(m32["rho"], m64["rho"], pr.rho_g, pr.rho_l)
+    assert np.max(np.abs(shift)) < 2e-4
+    assert np.max(np.abs(m32["rho"] - m64["rho"])) < 5e-5
+    aligned = _shift(m32["rho"], -shift[0], -shift[1])
+    assert np.max(np.abs(aligned - m64["rho"])) < 1e-5
+    for yx in ((128, 128), (0, 0)):
+        assert abs(m32["rho"][yx] - m64["rho"][yx]) < 1e-6
+    assert abs(s32["umax"] - s64["umax"]) < 1e-3 * s64["umax"]
     sigma = eq.surface_tension(pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
-    dp = eq.p0(rin, pr.beta, pr.rho_l, pr.rho_g) - eq.p0(rout, pr.beta, pr.rho_l, pr.rho_g)
-    assert abs(dp * radius / sigma - 1.0) < 0.02
-    assert rin > pr.rho_l and rout > pr.rho_g
+
+    def jump(m):
+        rin, rout = m["rho"][128, 128], m["rho"][0, 0]
+        return (eq.p0(rin, pr.beta, pr.rho_l, pr.rho_g)
+                - eq.p0(rout, pr.beta, pr.rho_l, pr.rho_g)) * radius / sigma
+
+    assert abs(jump(m32) - jump(m64)) < 1e-4
+    assert abs(jump(m32) - 1.0) < (0.05 if radius < 50 else 0.02)
+    assert m32["rho"][128, 128] > pr.rho_l and m32["rho"][0, 0] > pr.rho_g

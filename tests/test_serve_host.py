@@ -59,7 +59,7 @@ class FakeBatch:
 
     def info(self, cid):
         v = self.cases[cid]
-        return {"state": 1, "steps": v["steps"]}
+        return {"state": v.get("state", 1), "steps": v["steps"]}
 
     def retire(self, cid):
         del self.cases[cid]
@@ -181,3 +181,38 @@ def test_autotune_with_cases_that_stop_at_once(tmp_path, monkeypatch):
     out = autotune.tune(b, [(64, 64)], "FakeGPU", candidates=cands, launches=2)
     assert out["config"] == [64, 16, 8] and out["mlups"] is None and not out["cached"]
     assert b.cfg == (64, 16, 8) and not (tmp_path / "tune.json").exists()
+
+
+class OutcomeBatch(FakeBatch):
+    """Case k's outcome state is outcomes[k % len(outcomes)]."""
+
+    def __init__(self, slots, outcomes):
+        super().__init__(slots)
+        self.outcomes = outcomes
+
+    def admit(self, params, rho, tol, max_steps):
+        cid = super().admit(params, rho, tol, max_steps)
+        if cid is not None:
+            self.cases[cid]["state"] = self.outcomes[cid % len(self.outcomes)]
+        return cid
+
+
+def test_latency_is_split_by_outcome_and_stop_after():
+    """Converged, budget-exhausted and unstable requests are counted and
+    timed separately; converged step counts are reported; stop_after ends
+    the run once that many requests have completed."""
+    b = OutcomeBatch(slots=16, outcomes=[serve.CONVERGED, serve.UNSTABLE, serve.CONVERGED,
+                                         serve.BUDGET])
+    srv = serve.Server(b, clock=FakeClock())
+    reqs = [_req(k, 0.0, 1 + k) for k in range(12)]
+    rep = srv.run(reqs, duration=1e9, stop_after=8)
+    s = rep.summary()
+    assert s["completed"] >= 8 and s["completed"] < 12
+    n = {name: s[f"{name}_count"] for name in serve.OUTCOMES.values()}
+    assert sum(n.values()) == s["completed"]
+    assert n["converged"] == sum(1 for r in rep.completed if r.state == serve.CONVERGED) > 0
+    assert n["unstable"] > 0 and n["budget"] > 0
+    conv = rep.latencies(serve.CONVERGED)
+    assert s["converged_p50_latency_s"] == float(np.percentile(conv, 50))
+    steps = [r.steps for r in rep.completed if r.state == serve.CONVERGED]
+    assert s["converged_p99_steps"] == float(np.percentile(steps, 99))
