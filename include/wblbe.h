@@ -361,6 +361,15 @@ const char* wblbe_noalloc_last_error(void);
 wblbe_status wblbe_probe_fp64_fma(double* out, int32_t blocks, int32_t threads,
                                   int32_t iters, void* cuda_stream);
 
+/* Measurement aid (no counterpart in the paper): the reciprocal 1/rho that
+ * the float64 update uses for u = (sum_i c_i f_i + F/2) / rho (Eq. rhoU),
+ * evaluated on n device values x: seed[i] = the hardware approximation it
+ * starts from, refined[i] = the refined reciprocal the kernels use (either
+ * output may be NULL, not both).  Device arrays of n doubles, owned by the
+ * caller; asynchronous on cuda_stream.  EINVAL on bad arguments. */
+wblbe_status wblbe_probe_reciprocal(const double* x, double* seed, double* refined,
+                                    int64_t n, void* cuda_stream);
+
 /* Debugging aid (no counterpart in the paper).  Compute-sanitizer is not
  * available where this library is tested, so a build with
  * -DWBLBE_DEBUG_BOUNDS checks every global access of the step, moments and

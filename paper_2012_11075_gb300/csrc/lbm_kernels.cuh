@@ -116,14 +116,34 @@ __device__ __forceinline__ T chem_pot(T c, T e, T w, T n, T s, T ne, T nw, T se,
 }
 
 // 1/x: the hardware reciprocal approximation in FP32 (about 1 ulp; the FP32
-// path's error budget is set by float storage anyway), the IEEE division in
-// FP64.
+// path's error budget is set by float storage anyway).
 __device__ __forceinline__ float recip(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// The hardware's FP64 reciprocal approximation (rcp.approx.ftz.f64), the
+// seed of recip(double).
+__device__ __forceinline__ double recip_seed(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+
+// 1/x in FP64 for the density (normal, positive in any valid state): the
+// hardware seed r, then one step of the third-order Householder iteration
+// for the reciprocal, r <- r + r (e + e^2) with e = 1 - x r (two fused
+// multiply-adds and one more for the update), which cubes the seed's
+// relative error.  Three FP64 instructions after the seed, where the IEEE
+// division takes several more and a slow-path test; its accuracy against
+// the IEEE quotient is checked on the GPU (wblbe_probe_reciprocal).  A zero
+// or non-finite x gives a non-finite result.
+__device__ __forceinline__ double recip(double x) {
+  const double r = recip_seed(x);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
 
 // Collision constants in the arithmetic type, converted once per kernel (a
 // float <- double conversion inside the row loop would run on the FP64 pipe).
@@ -137,9 +157,10 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // 1 - omega is exact (Sterbenz); for smaller omega, omega is taken as 1 - keep.
 template <typename T>
 struct CollideConsts {
-  T omega, kf, keep, kf_m3, rho_ref, kappa;
+  T omega, kf, keep, kf_m3, rho_ref, kappa, kf12;
   __device__ explicit CollideConsts(const KParams& p)
-      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)) {
+      : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)),
+        kf12(T(p.kforce / 12.0)) {
     const T w = T(p.omega);
     if (w >= T(0.5)) {
       omega = w;
@@ -174,16 +195,35 @@ template <typename T>
 __device__ __forceinline__ void textbook_pairs(T (&g)[9], T rs, T rho, T ux, T uy, T Fx,
                                                T Fy, const CollideConsts<T>& q);
 
-template <typename T, int SCH>
+// GS: the gradient inputs are GS times the gradients (12: the strip kernel
+// passes 12 grad, see iso_grad12, and the factor 1/12 is folded into the
+// few places that use them; 1: plain gradients).
+template <typename T, int SCH, int GS = 1>
 __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
                                         T gry, const CollideConsts<T>& q, T& ux_out,
                                         T& uy_out) {
   constexpr bool WB = SCH == kSchWB;
   constexpr bool kShifted = sizeof(T) == 4;   // FP32 storage is always shifted
+  constexpr bool kG12 = GS == 12;
+  static_assert(GS == 1 || GS == 12, "gradient scale");
   const T omega = q.omega, kf = q.kf;
-  const T rho = rs + q.rho_ref;
+  // FP64 storage is unshifted (rho_ref = 0)
+  const T rho = kShifted ? rs + q.rho_ref : rs;
   T Fx, Fy;
-  if (WB) {
+  if (kG12) {
+    const T nr = rho * T(-1.0 / 12.0);                   // -rho / 12
+    if (WB) {
+      Fx = nr * gmx;                                     // Eq. mF
+      Fy = nr * gmy;
+    } else if (SCH == kSchPressure) {
+      const T kr = q.kappa * rho;                        // pressure form
+      Fx = T(1.0 / 12.0) * (grx + kr * gmx);
+      Fy = T(1.0 / 12.0) * (gry + kr * gmy);
+    } else {
+      Fx = T(1.0 / 36.0) * grx + nr * gmx;               // potential form
+      Fy = T(1.0 / 36.0) * gry + nr * gmy;
+    }
+  } else if (WB) {
     Fx = -rho * gmx;                                     // Eq. mF
     Fy = -rho * gmy;
   } else if (SCH == kSchPressure) {
@@ -208,8 +248,8 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
 
   T Gx = Fx, Gy = Fy;
   if (WB) {
-    Gx = Fx + T(1.0 / 3.0) * grx;
-    Gy = Fy + T(1.0 / 3.0) * gry;
+    Gx = Fx + T(kG12 ? 1.0 / 36.0 : 1.0 / 3.0) * grx;
+    Gy = Fy + T(kG12 ? 1.0 / 36.0 : 1.0 / 3.0) * gry;
   }
   const T orho = omega * rho;
   const T uu = ux * ux + uy * uy;
@@ -218,7 +258,7 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
 
   T E0, Cax, Cdg;
   if (WB) {
-    const T ku = kf * (ux * grx + uy * gry);
+    const T ku = (kG12 ? q.kf12 : kf) * (ux * grx + uy * gry);
     E0 = T(4.0 / 9.0) * (t - ku);
     Cax = T(1.0 / 9.0) * (t + T(0.5) * ku);
     Cdg = T(1.0 / 36.0) * (t + T(2) * ku);
@@ -322,6 +362,16 @@ __device__ __forceinline__ void iso_grad(T e, T w, T n, T s, T ne, T nw, T se, T
   const T d1 = ne - sw, d2 = se - nw;
   gx = T(1.0 / 3.0) * (e - w) + T(1.0 / 12.0) * (d1 + d2);
   gy = T(1.0 / 3.0) * (n - s) + T(1.0 / 12.0) * (d1 - d2);
+}
+
+// 12 times the same gradient, 4 (E - W) + (d1 + d2): two multiplications
+// fewer per gradient; collide<T, SCH, 12> folds the 1/12 into its uses.
+template <typename T>
+__device__ __forceinline__ void iso_grad12(T e, T w, T n, T s, T ne, T nw, T se, T sw,
+                                           T& gx, T& gy) {
+  const T d1 = ne - sw, d2 = se - nw;
+  gx = T(4) * (e - w) + (d1 + d2);
+  gy = T(4) * (n - s) + (d1 - d2);
 }
 
 // ---- packed FP32 pairs ------------------------------------------------------
@@ -592,6 +642,29 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
                : "memory");
 }
+// The same 16-byte copy with an L2 eviction-priority hint (a policy made by
+// createpolicy): the batched kernel keeps the halo rows that a neighbouring
+// tile reads later in L2 with it (see strip_pass).
+__device__ __forceinline__ void cp_async16_hint(void* smem, const void* gmem, uint64_t policy) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)),
+               "l"(gmem), "l"(policy)
+               : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -847,17 +920,41 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   int row_p = ((req_rw == p.ny - 1) ? 0 : req_rw + 1) * p.pitch;
   int row_0 = req_rw * p.pitch;
   int row_m = ((req_rw == 0) ? p.ny - 1 : req_rw - 1) * p.pitch;
+  // Rows kfirst .. kfirst + nlast are processed in groups of R (a row past
+  // klast only feeds values nobody reads).
+  const int ngroups = (klast - kfirst + R) / R;
+  const int nlast = R * ngroups - 1;       // last row, relative to kfirst
+  // Batched tiles (GHOST): the first rows a tile stages are the halo of the
+  // tile below it, which reads them at the end of its own march, after the
+  // L2 has seen the rest of both tiles go by.  They are staged with the
+  // evict-last priority; the tile's last rows, which the tile above has
+  // already read at its start, with evict-first; the rest with the normal
+  // priority.
+  constexpr int kHintRows = 6;
+  int nreq = 0;
+  uint64_t pol_last = 0, pol_first = 0, pol_normal = 0;
+  if (GHOST) {
+    pol_last = l2_policy_evict_last();
+    pol_first = l2_policy_evict_first();
+    pol_normal = l2_policy_evict_normal();
+  }
   auto request_next = [&](int slot) {
     T* st = stage + slot * 9 * SW;
     if (use_vec) {
+      const uint64_t pol = nreq < kHintRows ? pol_last
+                                            : (nreq > nlast - kHintRows ? pol_first : pol_normal);
 #pragma unroll
       for (int cls = 0; cls < 3; ++cls) {
         const int roff = cls == 0 ? row_0 : (cls == 1 ? row_m : row_p);
 #pragma unroll
         for (int m = 0; m < CPT; ++m)
           if (ch_on[cls][m] && WB_IN(ch_src[cls][m] + roff - src, 9 * p.plane - (E - 1)) &&
-              WB_IN(ch_dst[cls][m], 9 * SW - (E - 1)))
-            cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
+              WB_IN(ch_dst[cls][m], 9 * SW - (E - 1))) {
+            if (GHOST)
+              cp_async16_hint(st + ch_dst[cls][m], ch_src[cls][m] + roff, pol);
+            else
+              cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
+          }
       }
     } else {
       const int ncols = w + 2 * kPad;
@@ -871,6 +968,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
         }
       }
     }
+    ++nreq;
     req_rw = (req_rw + 1 == p.ny) ? 0 : req_rw + 1;
     row_m = row_0;
     row_0 = row_p;
@@ -884,10 +982,6 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   };
 
 
-  // Rows kfirst .. kfirst + nlast are processed in groups of R (a row past
-  // klast only feeds values nobody reads).
-  const int ngroups = (klast - kfirst + R) / R;
-  const int nlast = R * ngroups - 1;       // last row, relative to kfirst
 
   // store position of column x0 + tx within a plane; ghost copies a boundary
   // column also writes: x < 4 -> +nx (right ghost), x >= nx - 4 -> -nx (left)
@@ -1046,13 +1140,14 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
               if (own) {
                 mrow[sx] = at(sx);
                 frs[j] = rc[sx];
+                // 12 grad(rho) (or 12 grad(cs^2 rho - p_0)): see iso_grad12
                 if (kPress)
-                  iso_grad<T>(press_a(rc[sx + 1]), press_a(rc[sx - 1]), press_a(rn[sx]),
-                              press_a(rsb[sx]), press_a(rn[sx + 1]), press_a(rn[sx - 1]),
-                              press_a(rsb[sx + 1]), press_a(rsb[sx - 1]), fgx[j], fgy[j]);
+                  iso_grad12<T>(press_a(rc[sx + 1]), press_a(rc[sx - 1]), press_a(rn[sx]),
+                                press_a(rsb[sx]), press_a(rn[sx + 1]), press_a(rn[sx - 1]),
+                                press_a(rsb[sx + 1]), press_a(rsb[sx - 1]), fgx[j], fgy[j]);
                 else
-                  iso_grad<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
-                              rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+                  iso_grad12<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
+                                rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
               }
               if (tx == mu_lo) mrow[3] = at(3);
               if (tx == mu_hi && WB_IN(w + 4, SW)) mrow[w + 4] = at(w + 4);
@@ -1121,9 +1216,9 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
               const T* m_c = mu_s + WB_SLOT(j - 2, kMuRing) * SW;
               const T* m_up = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
               // "up" is row c+1 (+y), "dn" row c-1; slot sx+1 is +x
-              T gmx, gmy;
-              iso_grad<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1],
-                          m_up[sx - 1], m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
+              T gmx, gmy;                        // 12 grad(mu)
+              iso_grad12<T>(m_c[sx + 1], m_c[sx - 1], m_up[sx], m_dn[sx], m_up[sx + 1],
+                            m_up[sx - 1], m_dn[sx + 1], m_dn[sx - 1], gmx, gmy);
               const T rs = j == 0 ? prs : frs[j - 1];
               const T grx = j == 0 ? pgx : fgx[j - 1];
               const T gry = j == 0 ? pgy : fgy[j - 1];
@@ -1133,7 +1228,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                         st[3 * SW + sx + 1], st[4 * SW + sx],     st[5 * SW + sx - 1],
                         st[6 * SW + sx + 1], st[7 * SW + sx + 1], st[8 * SW + sx - 1]};
               T ux, uy;
-              collide<T, SCH>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
+              collide<T, SCH, 12>(g, rs, gmx, gmy, grx, gry, cc, ux, uy);
               emit_node<T, MODE, GHOST>(p, mo, dst, c, xcol, xm, ghost_r, ghost_l, g, rs,
                                         STATS ? mu_node(rs, m_c[sx]) : T(0), ux, uy, acc, acc_on);
             }

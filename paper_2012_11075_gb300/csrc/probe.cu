@@ -9,8 +9,17 @@
 #include <cuda_runtime.h>
 
 #include "../../include/wblbe.h"
+#include "lbm_kernels.cuh"
 
 namespace {
+
+__global__ void reciprocal_kernel(const double* __restrict__ x, double* __restrict__ seed,
+                                  double* __restrict__ refined, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (seed) seed[i] = wblbe::recip_seed(x[i]);
+  if (refined) refined[i] = wblbe::recip(x[i]);
+}
 
 constexpr int kChains = 8;
 
@@ -38,5 +47,16 @@ extern "C" wblbe_status wblbe_probe_fp64_fma(double* out, int32_t blocks, int32_
   if (!out || blocks < 1 || threads < 32 || threads > 1024 || (threads % 32) != 0 || iters < 1)
     return WBLBE_EINVAL;
   fp64_fma_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(out, iters);
+  return cudaGetLastError() == cudaSuccess ? WBLBE_OK : WBLBE_ECUDA;
+}
+
+extern "C" wblbe_status wblbe_probe_reciprocal(const double* x, double* seed, double* refined,
+                                               int64_t n, void* cuda_stream) {
+  if (!x || n < 0 || (!seed && !refined)) return WBLBE_EINVAL;
+  if (n == 0) return WBLBE_OK;
+  const long long blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffffLL) return WBLBE_EINVAL;
+  reciprocal_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
+      x, seed, refined, (long long)n);
   return cudaGetLastError() == cudaSuccess ? WBLBE_OK : WBLBE_ECUDA;
 }

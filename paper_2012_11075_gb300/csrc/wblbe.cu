@@ -72,8 +72,11 @@ Layout make_layout(const wblbe_params* p) {
   L.pitch = (p->nx + align_elems - 1) / align_elems * align_elems;
   L.plane = (long long)L.pitch * p->ny;
   L.pops_bytes = align_up((size_t)9 * (size_t)L.plane * L.elem);
+  // per-CTA records: the moments pass (32-column strips at the narrowest,
+  // kMomentsRows rows) and a step with statistics in any default launch
+  // shape (at least 32 columns and 8 rows per CTA)
   const int strips = (p->nx + 31) / 32;
-  const int runs = (p->ny + kMomentsRows - 1) / kMomentsRows;
+  const int runs = (p->ny + 7) / 8;
   L.max_partials = strips * runs;
   size_t off = 0;
   L.off_a = off; off += L.pops_bytes;

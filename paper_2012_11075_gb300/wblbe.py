@@ -128,6 +128,7 @@ _SIGNATURES = {
     "wblbe_debug_bounds_errors": (ctypes.c_uint, [ctypes.c_int32]),
     "wblbe_probe_fp64_fma": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             _P]),
+    "wblbe_probe_reciprocal": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P]),
 }
 
 _lib = None

@@ -66,11 +66,17 @@ def _shift(field, dx, dy):
 
 def test_fp32_flat_slab_against_fp64_and_discrete_equilibrium():
     """Odd slab 4 x 201 (W = 4, ratio 10, tau = 1.0) from the tanh profile,
-    50000 steps: the FP32 profile within 2e-6 of the FP64 run's, both near
-    the Newton solution of the discrete balance (still relaxing), velocity
-    below 1e-7, the slab's mean velocity below 1e-8, the mass within 1e-6
-    (804 nodes: the random walk of the rounding is largest on small
-    lattices)."""
+    50000 steps, FP32 against the FP64 run.  The rounding noise moves the
+    slab as a whole (a random walk of its position) and feeds the
+    x-alternating density pattern, an exact stationary state of the
+    well-balanced scheme (its central gradients vanish, so it feels no
+    force); both stay at the size of a random walk of the rounding.  So the
+    x-averaged profile is compared: within 1e-4 of FP64's as it is (drift
+    included), within 5e-6 once the drift is removed, and the x-alternation
+    below 5e-6.  Also: the mass within 1e-6 (804 nodes: the random walk is
+    largest on small lattices), the slab's mean velocity below 1e-8, max|u|
+    below 1e-7, both precisions within 2e-4 of the Newton solution of the
+    discrete balance (still relaxing at this step count)."""
     pr = wl.flat_interface(nx=4, ny=201)
     pr.tau = 1.0
     rN, _ = eq.discrete_flat_equilibrium(pr.rho[:, 0], pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
@@ -78,8 +84,13 @@ def test_fp32_flat_slab_against_fp64_and_discrete_equilibrium():
     m64, s64 = _run(pr, wblbe.FP64, 50000)
     r = m32["rho"]
     assert abs(s32["mass_drift_rel"]) < 1e-6
-    assert np.max(np.abs(r - m64["rho"])) < 2e-6
-    assert np.max(np.abs(m64["rho"][:, 0] - rN)) < 1e-4 and np.max(np.abs(r[:, 0] - rN)) < 1e-4
+    p32, p64 = r.mean(axis=1), m64["rho"].mean(axis=1)
+    assert np.max(np.abs(r - p32[:, None])) < 5e-6
+    assert np.max(np.abs(p32 - p64)) < 1e-4
+    dy = _centroid_shift(p32[:, None], p64[:, None], pr.rho_g, pr.rho_l)[1]
+    aligned = _shift(p32[:, None], 0.0, -dy)[:, 0]
+    assert np.max(np.abs(aligned - p64)) < 5e-6, (dy, np.max(np.abs(aligned - p64)))
+    assert np.max(np.abs(p64 - rN)) < 2e-4 and np.max(np.abs(p32 - rN)) < 2e-4
     U = (r * m32["uy"]).sum() / r.sum()
     assert abs(U) < 1e-8
     assert s32["umax"] < 1e-7
@@ -111,7 +122,10 @@ def test_fp32_droplet_against_fp64_long_run(radius):
     droplet's centroid within 2e-4 lattice units, the density field within
     5e-5 and, with the centroid shift removed, within 1e-5; bulk densities
     within 1e-6, max|u| within 0.1 %, the Laplace jump Delta p R / sigma
-    within 1e-4 of FP64's and within the O(W/R) window of 1."""
+    within 1e-4 of FP64's and within the O(W/R) window of 1.  The bulk
+    densities are averages over the inner disk r < R/2 and over the nodes
+    farther than R + 3W from the centre: at a single node the FP32 density
+    carries about 1e-7 of rounding noise."""
     pr = wl.droplet(n=256, radius=radius, tau=1.0)
     m32, s32 = _run(pr, wblbe.FP32_SHIFTED, 100000)
     m64, s64 = _run(pr, wblbe.FP64, 100000)
@@ -121,16 +135,20 @@ def test_fp32_droplet_against_fp64_long_run(radius):
     assert np.max(np.abs(m32["rho"] - m64["rho"])) < 5e-5
     aligned = _shift(m32["rho"], -shift[0], -shift[1])
     assert np.max(np.abs(aligned - m64["rho"])) < 1e-5
-    for yx in ((128, 128), (0, 0)):
-        assert abs(m32["rho"][yx] - m64["rho"][yx]) < 1e-6
+    yy, xx = np.mgrid[0:256, 0:256]
+    r = np.hypot(xx - 128, yy - 128)
+    inner, outer = r < radius / 2, r > radius + 12
+    bulk = {k: (m["rho"][inner].mean(), m["rho"][outer].mean())
+            for k, m in (("32", m32), ("64", m64))}
+    assert abs(bulk["32"][0] - bulk["64"][0]) < 1e-6
+    assert abs(bulk["32"][1] - bulk["64"][1]) < 1e-6
     assert abs(s32["umax"] - s64["umax"]) < 1e-3 * s64["umax"]
     sigma = eq.surface_tension(pr.kappa, pr.beta, pr.rho_l, pr.rho_g)
 
-    def jump(m):
-        rin, rout = m["rho"][128, 128], m["rho"][0, 0]
+    def jump(rin, rout):
         return (eq.p0(rin, pr.beta, pr.rho_l, pr.rho_g)
                 - eq.p0(rout, pr.beta, pr.rho_l, pr.rho_g)) * radius / sigma
 
-    assert abs(jump(m32) - jump(m64)) < 1e-4
-    assert abs(jump(m32) - 1.0) < (0.05 if radius < 50 else 0.02)
-    assert m32["rho"][128, 128] > pr.rho_l and m32["rho"][0, 0] > pr.rho_g
+    assert abs(jump(*bulk["32"]) - jump(*bulk["64"])) < 1e-4
+    assert abs(jump(*bulk["32"]) - 1.0) < (0.05 if radius < 50 else 0.02)
+    assert bulk["32"][0] > pr.rho_l and bulk["32"][1] > pr.rho_g
