@@ -318,6 +318,56 @@ int64_t wblbe_batch_kernel_launches(wblbe_batch_handle b);
 wblbe_status wblbe_batch_destroy(wblbe_batch_handle b);
 const char* wblbe_batch_last_error(wblbe_batch_handle b);
 
+/* ---- one lattice split into row slabs ------------------------------------
+ * The update of Eq. D2Q9 is local: one step of a node reads the
+ * post-collision populations of the previous step within 3 nodes of it (the
+ * pulled populations, the densities that mu and its gradient need: Sec. II).
+ * So a lattice can be split into slabs of whole rows, each advanced from its
+ * own rows and 3 ghost rows on each side, with one exchange of ghost rows
+ * per step.  These entry points do that on one device: nslabs slabs of
+ * near-equal row counts (boundaries on even rows, every slab >= 3 rows),
+ * stepped by the single-lattice kernels and exchanged by device-to-device
+ * copies, with results equal bit for bit to a wblbe_create handle of the
+ * same parameters (schemes 0-3; the E6 variant is refused).  Conventions,
+ * arrays, workspace and stream rules are those of the single-lattice API. */
+typedef struct wblbe_slabs* wblbe_slabs_handle;
+
+/* First global row of every slab: row_starts[k] for k = 0..nslabs
+ * (row_starts[nslabs] = ny); host only.  EINVAL if a slab would have fewer
+ * than 3 rows. */
+wblbe_status wblbe_slabs_rows(int32_t ny, int32_t nslabs, int32_t* row_starts);
+
+/* Device workspace bytes for a split into nslabs slabs; 0 if invalid. */
+size_t wblbe_slabs_workspace_bytes(const wblbe_params* params, int32_t nslabs);
+
+/* Create a split lattice (workspace borrowed until destroy).  EINVAL on
+ * bad parameters, scheme 4, too many slabs or a short/misaligned workspace
+ * (ENOMEM when only short). */
+wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs,
+                                void* dev_workspace, size_t workspace_bytes,
+                                void* cuda_stream, wblbe_slabs_handle* out);
+
+/* As wblbe_init_rho: u = 0, f = f^eq(rho, 0); rho [ny][nx] float64. */
+wblbe_status wblbe_slabs_init_rho(wblbe_slabs_handle h, const double* rho,
+                                  int32_t rho_on_device);
+
+/* Advance nsteps steps (every slab, then the ghost-row exchange). */
+wblbe_status wblbe_slabs_step(wblbe_slabs_handle h, int64_t nsteps);
+
+/* As wblbe_moments, for the whole lattice (fields [ny][nx], each may be
+ * NULL; stats reduced over all slabs in a fixed order).  Synchronises. */
+wblbe_status wblbe_slabs_moments(wblbe_slabs_handle h, double* rho, double* ux,
+                                 double* uy, double* mu, int32_t out_on_device,
+                                 wblbe_stats* stats);
+
+/* The whole lattice's populations f_i(x, t) as [9][ny][nx] float64. */
+wblbe_status wblbe_slabs_get_populations(wblbe_slabs_handle h, double* f,
+                                         int32_t on_device);
+int64_t wblbe_slabs_step_count(wblbe_slabs_handle h);
+int64_t wblbe_slabs_kernel_launches(wblbe_slabs_handle h);
+wblbe_status wblbe_slabs_destroy(wblbe_slabs_handle h);
+const char* wblbe_slabs_last_error(wblbe_slabs_handle h);
+
 /* ---- allocation-free statistics pass ------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
  * cannot allocate device memory at all: hosts whose own allocator has

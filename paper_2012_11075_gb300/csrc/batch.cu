@@ -404,6 +404,9 @@ KParams case_kparams(const wblbe_batch::Case& c, int rows) {
   k.dl = rr - p.rho_l;
   k.dg = rr - p.rho_g;
   k.step = c.steps;                        // advanced on the device by each launch
+  k.row_lo = 0;
+  k.row_hi = p.ny;
+  k.y_offset = 0;
   return k;
 }
 

@@ -48,6 +48,12 @@ struct KParams {
   // (step_base may be null; a graph replay reads its base from device memory).
   long long step;
   const long long* step_base;
+  // Rows of the stored lattice a step or moments launch updates, [row_lo,
+  // row_hi) (the whole lattice: 0, ny), and the offset from a stored row to
+  // its row in the global lattice (0, except for a slab of a lattice split
+  // into row slabs: there the stored rows are the slab's rows and the ghost
+  // rows around them).
+  int row_lo, row_hi, y_offset;
 };
 
 // Outputs of the moments mode (any pointer may be null).
@@ -797,7 +803,7 @@ __device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo
     const double mu = (double)muc;
     const double dux = (double)ux, duy = (double)uy;
     if (MOMENTS && WB_IN(c, p.ny) && WB_IN(xm, p.nx)) {
-      const unsigned kk = (unsigned)(c * p.nx + xm);
+      const unsigned kk = (unsigned)((c + p.y_offset) * p.nx + xm);
       if (mo.rho) mo.rho[kk] = rho;
       if (mo.ux) mo.ux[kk] = dux;
       if (mo.uy) mo.uy[kk] = duy;
@@ -1180,11 +1186,12 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                            V(s0, s1, 6 * SW + sx + 1), V(s0, s1, 7 * SW + sx + 1),
                            V(s0, s1, 8 * SW + sx - 1)};
             float2 ux, uy;
-            // draws of rows c0 and c0 + 1 (one hash when c0 is even, the
-            // usual case; the parity of c0 is fixed within a CTA)
-            const uint32_t kx = (uint32_t)c0 * (uint32_t)p.nx + (uint32_t)xm;
+            // draws of rows c0 and c0 + 1 (one hash when the global row of
+            // c0 is even, the usual case; its parity is fixed within a CTA)
+            const int cg = c0 + p.y_offset;
+            const uint32_t kx = (uint32_t)cg * (uint32_t)p.nx + (uint32_t)xm;
             float2 rnd;
-            if ((c0 & 1) == 0) {
+            if ((cg & 1) == 0) {
               rnd = pair_uniforms(kx, ht);
             } else {
               rnd = make_float2(pair_uniforms(kx - (uint32_t)p.nx, ht).y,
@@ -1286,7 +1293,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 }
 
 // One CTA per strip segment: blockIdx.x picks the strip, blockIdx.y the run
-// of p.rows rows.  MODE is a StripMode: the moments mode, and the step with
+// of p.rows rows (from p.row_lo).  MODE is a StripMode: the moments mode, and the step with
 // statistics (a step that also reduces the stats of the state it starts
 // from), write the per-CTA stats record.
 template <typename T, int SCH, int MODE, int TX>
@@ -1295,8 +1302,8 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks(TX))
                      const KParams p, const MomentsOut mo) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int x0 = blockIdx.x * TX;
-  const int y0 = blockIdx.y * p.rows;
-  const int y1 = min(y0 + p.rows, p.ny);
+  const int y0 = p.row_lo + blockIdx.y * p.rows;
+  const int y1 = min(y0 + p.rows, p.row_hi);
   double* rec = (MODE != kModeStep && mo.partials)
                     ? mo.partials + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * kStatRec
                     : nullptr;

@@ -47,7 +47,7 @@ cudaError_t allow_smem_scheme() {
 template <typename T, int SCH, int MOM, int TX>
 cudaError_t launch_tx(const void* src, void* dst, const KParams& kp, const MomentsOut& mo,
                       cudaStream_t s) {
-  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + kp.rows - 1) / kp.rows);
+  dim3 grid((kp.nx + TX - 1) / TX, (kp.row_hi - kp.row_lo + kp.rows - 1) / kp.rows);
   lbm_strip_kernel<T, SCH, MOM, TX><<<grid, TX, strip_smem<T>(TX), s>>>(
       static_cast<const T*>(src), static_cast<T*>(dst), kp, mo);
   return cudaGetLastError();
@@ -117,6 +117,12 @@ constexpr int kSchE6 = 4;
 cudaError_t launch_e6(int mode, const void* src, void* dst, const KParams& kp,
                       const MomentsOut& mo, cudaStream_t s);
 int e6_partials(int nx, int ny);
+// Strip-kernel launches for scheme codes 0-3 without instantiating the
+// kernel templates again (defined in wblbe.cu; used by slabs.cu).
+cudaError_t launch_strip_any(int sch, bool fp64, int mode, const void* src, void* dst,
+                             const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s);
+int resident_strip_any(int sch, bool fp64, int tile);
+cudaError_t allow_smem_strip_all();
 // Bounds-check counts of the other translation units (bounds-checked build).
 unsigned int variants_bounds_errors(bool reset);
 unsigned int batch_bounds_errors(bool reset);

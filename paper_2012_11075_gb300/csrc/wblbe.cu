@@ -168,6 +168,9 @@ KParams make_kparams(const wblbe_ctx* h, int rows) {
   k.rho_ref = rr;
   k.dl = rr - p.rho_l;
   k.dg = rr - p.rho_g;
+  k.row_lo = 0;
+  k.row_hi = p.ny;
+  k.y_offset = 0;
   return k;
 }
 
@@ -390,6 +393,32 @@ dim3 layout_grid(const wblbe_ctx* h) {
 }
 
 }  // namespace
+
+namespace wblbe {
+
+cudaError_t launch_strip_any(int sch, bool fp64, int mode, const void* src, void* dst,
+                             const KParams& kp, const MomentsOut& mo, int tile, cudaStream_t s) {
+  switch (sch) {
+    case WBLBE_STANDARD: return launch_scheme<kSchStandard>(fp64, mode, src, dst, kp, mo, tile, s);
+    case WBLBE_WELL_BALANCED: return launch_scheme<kSchWB>(fp64, mode, src, dst, kp, mo, tile, s);
+    case WBLBE_STANDARD_PRESSURE:
+    case WBLBE_STANDARD_TEXTBOOK:
+      return launch_variant(sch, fp64, mode, src, dst, kp, mo, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int resident_strip_any(int sch, bool fp64, int tile) {
+  switch (sch) {
+    case WBLBE_STANDARD: return resident_scheme<kSchStandard>(fp64, tile);
+    case WBLBE_WELL_BALANCED: return resident_scheme<kSchWB>(fp64, tile);
+    default: return resident_variant(sch, fp64, tile);
+  }
+}
+
+cudaError_t allow_smem_strip_all() { return allow_smem_all(); }
+
+}  // namespace wblbe
 
 extern "C" {
 

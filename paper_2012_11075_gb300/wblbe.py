@@ -122,6 +122,20 @@ _SIGNATURES = {
     "wblbe_batch_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_batch_destroy": (ctypes.c_int, [_H]),
     "wblbe_batch_last_error": (ctypes.c_char_p, [_H]),
+    "wblbe_slabs_rows": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]),
+    "wblbe_slabs_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CParams), ctypes.c_int32]),
+    "wblbe_slabs_create": (ctypes.c_int, [ctypes.POINTER(CParams), ctypes.c_int32, _P,
+                                          ctypes.c_size_t, _P, ctypes.POINTER(_H)]),
+    "wblbe_slabs_init_rho": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
+    "wblbe_slabs_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "wblbe_slabs_moments": (ctypes.c_int, [_H, _P, _P, _P, _P, ctypes.c_int32,
+                                           ctypes.POINTER(CStats)]),
+    "wblbe_slabs_get_populations": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
+    "wblbe_slabs_step_count": (ctypes.c_int64, [_H]),
+    "wblbe_slabs_kernel_launches": (ctypes.c_int64, [_H]),
+    "wblbe_slabs_destroy": (ctypes.c_int, [_H]),
+    "wblbe_slabs_last_error": (ctypes.c_char_p, [_H]),
     "wblbe_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(CParams), _P, _P, _P, _P, _P,
                                              ctypes.POINTER(CStats), _P]),
     "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
@@ -489,3 +503,93 @@ def debug_bounds_errors(reset: bool = False) -> int:
     """Out-of-bounds accesses seen by a bounds-checked build of the library
     on the current device (0xFFFFFFFF: the loaded library has no checks)."""
     return int(load_library().wblbe_debug_bounds_errors(1 if reset else 0))
+
+
+def slab_rows(ny: int, nslabs: int) -> list:
+    """First global row of every slab of a lattice split into nslabs row
+    slabs (the library's partition; the last entry is ny).  Host only."""
+    out = (ctypes.c_int32 * (nslabs + 1))()
+    st = load_library().wblbe_slabs_rows(int(ny), int(nslabs), out)
+    if st != OK:
+        raise WblbeError(st, load_library().wblbe_slabs_last_error(None).decode())
+    return list(out)
+
+
+class Slabs:
+    """One lattice split into row slabs on the current CUDA device, each
+    advanced with 3 ghost rows on each side that are exchanged every step
+    (wblbe_slabs_*).  Same interface and results as Solver."""
+
+    def __init__(self, params: Params, nslabs: int, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.params = params
+        self.nslabs = int(nslabs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._cp = params.c()
+        nbytes = int(self.lib.wblbe_slabs_workspace_bytes(ctypes.byref(self._cp), self.nslabs))
+        if nbytes == 0:
+            raise WblbeError(EINVAL, "invalid parameters or slab count")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        st = self.lib.wblbe_slabs_create(ctypes.byref(self._cp), self.nslabs,
+                                         ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise WblbeError(st, self.lib.wblbe_slabs_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st: int) -> int:
+        if st != OK:
+            raise WblbeError(st, self.lib.wblbe_slabs_last_error(self.h).decode())
+        return st
+
+    @property
+    def shape(self):
+        return (self.params.ny, self.params.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._check(self.lib.wblbe_slabs_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_rho(self, rho):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        _require(rho.shape == self.shape, f"rho must have shape {self.shape}")
+        self._check(self.lib.wblbe_slabs_init_rho(self.h, ctypes.c_void_p(rho.ctypes.data), 0))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.wblbe_slabs_step(self.h, int(n)))
+
+    def moments(self):
+        st = CStats()
+        outs = [np.empty(self.shape) for _ in range(4)]
+        self._check(self.lib.wblbe_slabs_moments(self.h, *[ctypes.c_void_p(o.ctypes.data)
+                                                           for o in outs], 0, ctypes.byref(st)))
+        return dict(zip(("rho", "ux", "uy", "mu"), outs)), st.as_dict()
+
+    def stats(self) -> dict:
+        st = CStats()
+        self._check(self.lib.wblbe_slabs_moments(self.h, None, None, None, None, 1,
+                                                 ctypes.byref(st)))
+        return st.as_dict()
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((9,) + self.shape)
+        self._check(self.lib.wblbe_slabs_get_populations(self.h, ctypes.c_void_p(f.ctypes.data), 0))
+        return f
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.wblbe_slabs_step_count(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.wblbe_slabs_kernel_launches(self.h))
