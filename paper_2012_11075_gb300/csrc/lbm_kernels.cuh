@@ -402,8 +402,9 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 // rest population is g_0' = g_0 + (m - a), m and a the sums of the pulled
 // and of the post-collision moving populations.  In float storage the rest
 // population (about rho - rho_ref) is much larger than the moving ones
-// (O(u, F) in the well-balanced scheme), so the rounding of m, a and m - a is
-// far below an ulp of g_0, and one error-free addition (TwoSum) gives
+// (O(u, F) in the well-balanced scheme), so the roundings that enter m - a
+// (the moving populations' own, and those of the sums) are far below an
+// ulp of g_0, and one error-free addition (TwoSum) gives
 // g_0 + (m - a) = h + e exactly.  g_0' is h or its float neighbour on the
 // side of e, the neighbour with probability |e| / (distance to it): the
 // expected rounding error is zero, so a state that repeats its rounding step
@@ -448,19 +449,25 @@ __device__ __forceinline__ float2 pair_uniforms(uint32_t k, uint32_t ht) {
                      __fsub_rn(__uint_as_float(0x3f800000u | (h2 >> 9)), 1.0f));
 }
 
-// Round v = h + e (e the exact remainder, |e| at most half an ulp of h) to h
-// or to the float next to h on the side of e, choosing the neighbour with
-// probability |e| / gap (gap = the exact distance to it, a power of two);
-// u uniform in [0, 1) on a 2^-23 grid.  E[result] = v up to 2^-23 of a gap.
-// A zero, infinite or NaN h is returned unchanged.
-__device__ __forceinline__ float round_stochastic(float h, float e, float u) {
-  const uint32_t b = __float_as_uint(h);
-  // one step of the bit pattern away from zero when e and h have the same
-  // sign, towards zero otherwise
-  const bool away = (e > 0.0f) == (h > 0.0f);
-  const float n = __uint_as_float(away ? b + 1u : b - 1u);
-  const float gap = fabsf(__fsub_rn(n, h));
-  return (h != 0.0f && __fmul_rn(u, gap) < fabsf(e)) ? n : h;
+// The float next to h on the side of e: one step of the bit pattern away
+// from zero when e and h have the same sign bit, towards zero otherwise.
+// For a zero h it is a NaN or the smallest subnormal, for the largest finite
+// h an infinity (round_stochastic2 then keeps h or rounds to that tiny value).
+__device__ __forceinline__ float next_toward(float h, float e) {
+  const int b = __float_as_int(h);
+  const int s = (__float_as_int(e) ^ b) >> 31;        // 0: same sign, -1: opposite
+  return __int_as_float(b + 1 + 2 * s);
+}
+
+// Round v = h + e on a pair of lanes (e the exact remainder, |e| at most
+// half an ulp of h) to h or to the float next to h on the side of e,
+// choosing the neighbour with probability |e| / gap (gap = the exact
+// distance to it, a power of two); u uniform in [0, 1) on a 2^-23 grid.
+// E[result] = v up to 2^-23 of a gap.  An infinite or NaN h is kept.
+__device__ __forceinline__ float2 round_stochastic2(float2 h, float2 e, float2 u) {
+  const float2 n = make_float2(next_toward(h.x, e.x), next_toward(h.y, e.y));
+  const float2 ug = mul2(u, sub2(n, h));               // u times the signed gap
+  return make_float2(fabsf(ug.x) < fabsf(e.x) ? n.x : h.x, fabsf(ug.y) < fabsf(e.y) ? n.y : h.y);
 }
 
 // Mirror-symmetric sum of the eight moving populations: every lattice
@@ -615,10 +622,14 @@ __device__ __forceinline__ void collide_x2(float2 (&g)[9], float2 rs, float2 gmx
   g[6] = fma2(keep, g[6], add2(E6, O6));
   g[8] = fma2(keep, g[8], sub2(E6, O6));
   if (WB) {
-    // exact node mass balance g_0 + (m - a), stochastically rounded
+    // node mass balance g_0' = g_0 + (m - a), stochastically rounded.  The
+    // moving populations leave as keep g_i + (E +- O), so
+    // m - a = (1 - keep) m - 2 (E1 + E2 + E5 + E6) = omega m - 2 sum E, up to
+    // their own roundings, which are far below an ulp of g_0.
     float2 h, e;
-    two_sum2(g[0], sub2(m_in, moving_sum2(g)), h, e);
-    g[0] = make_float2(round_stochastic(h.x, e.x, rnd.x), round_stochastic(h.y, e.y, rnd.y));
+    const float2 se = add2(add2(E1, E2), add2(E5, E6));
+    two_sum2(g[0], fma2(splat(-2.0f), se, mul2(omega, m_in)), h, e);
+    g[0] = round_stochastic2(h, e, rnd);
   } else {
     // rest population from the node mass balance, as in the scalar version
     g[0] = sub2(rs, moving_sum2(g));

@@ -162,13 +162,17 @@ class Server:
             self.batch.retire(cid)
             self.report.completed.append(req)
 
-    def run(self, requests, duration: float, drain: bool = False, stop_after=None):
+    def run(self, requests, duration: float, drain: bool = False, stop_after=None,
+            time_cap=None):
         """Serve ``requests`` (sorted by arrival) in real time until
         ``duration`` seconds (and, with ``drain``, until all finished), or
-        until ``stop_after`` requests have completed, whichever comes first."""
+        until ``stop_after`` requests have completed, or ``time_cap`` seconds
+        have passed, whichever comes first."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         while True:
             if stop_after is not None and len(self.report.completed) >= stop_after:
+                break
+            if time_cap is not None and self.now() >= time_cap:
                 break
             t = self.now()
             while pending and pending[0].arrival <= t:

@@ -216,3 +216,16 @@ def test_latency_is_split_by_outcome_and_stop_after():
     assert s["converged_p50_latency_s"] == float(np.percentile(conv, 50))
     steps = [r.steps for r in rep.completed if r.state == serve.CONVERGED]
     assert s["converged_p99_steps"] == float(np.percentile(steps, 99))
+
+
+def test_time_cap_ends_a_drain():
+    """A drain stops at the time cap, leaving the unfinished requests
+    resident (reported as running at the end)."""
+    b = FakeBatch(slots=4)
+    clock = FakeClock()
+    srv = serve.Server(b, clock=clock)
+    reqs = [_req(k, 0.0, 10 ** 6 if k == 0 else 2) for k in range(3)]
+    rep = srv.run(reqs, duration=0.0, drain=True, time_cap=0.5)
+    s = rep.summary()
+    assert s["completed"] == 2 and s["running_at_end"] == 1
+    assert rep.elapsed >= 0.5
