@@ -15,11 +15,11 @@ import os
 import time
 from pathlib import Path
 
-# steps per launch 1-16 were never chosen on the benchmark mix; 24- and
-# 48-row tiles ranked within noise of 32 on the 64-case subsample but ran
-# slower on the full mix
-DEFAULT_CANDIDATES = [(tx, rows, k) for tx in (64, 128, 256) for rows in (16, 32, 64)
-                      for k in (8, 32, 64)]
+# strip width x rows per tile x steps per launch; 1-16 steps per launch were
+# never chosen on the benchmark mix (the per-launch host check and the
+# launch tail weigh too much)
+DEFAULT_CANDIDATES = [(tx, rows, k) for tx in (64, 128, 256) for rows in (16, 32, 64, 128)
+                      for k in (32, 64)]
 
 
 def cache_path() -> Path:

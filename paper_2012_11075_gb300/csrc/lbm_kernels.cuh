@@ -659,29 +659,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
                : "memory");
 }
-// The same 16-byte copy with an L2 eviction-priority hint (a policy made by
-// createpolicy): the batched kernel keeps the halo rows that a neighbouring
-// tile reads later in L2 with it (see strip_pass).
-__device__ __forceinline__ void cp_async16_hint(void* smem, const void* gmem, uint64_t policy) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)),
-               "l"(gmem), "l"(policy)
-               : "memory");
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_last() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_first() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
-  uint64_t p;
-  asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -941,37 +918,17 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   // klast only feeds values nobody reads).
   const int ngroups = (klast - kfirst + R) / R;
   const int nlast = R * ngroups - 1;       // last row, relative to kfirst
-  // Batched tiles (GHOST): the first rows a tile stages are the halo of the
-  // tile below it, which reads them at the end of its own march, after the
-  // L2 has seen the rest of both tiles go by.  They are staged with the
-  // evict-last priority; the tile's last rows, which the tile above has
-  // already read at its start, with evict-first; the rest with the normal
-  // priority.
-  constexpr int kHintRows = 6;
-  int nreq = 0;
-  uint64_t pol_last = 0, pol_first = 0, pol_normal = 0;
-  if (GHOST) {
-    pol_last = l2_policy_evict_last();
-    pol_first = l2_policy_evict_first();
-    pol_normal = l2_policy_evict_normal();
-  }
   auto request_next = [&](int slot) {
     T* st = stage + slot * 9 * SW;
     if (use_vec) {
-      const uint64_t pol = nreq < kHintRows ? pol_last
-                                            : (nreq > nlast - kHintRows ? pol_first : pol_normal);
 #pragma unroll
       for (int cls = 0; cls < 3; ++cls) {
         const int roff = cls == 0 ? row_0 : (cls == 1 ? row_m : row_p);
 #pragma unroll
         for (int m = 0; m < CPT; ++m)
           if (ch_on[cls][m] && WB_IN(ch_src[cls][m] + roff - src, 9 * p.plane - (E - 1)) &&
-              WB_IN(ch_dst[cls][m], 9 * SW - (E - 1))) {
-            if (GHOST)
-              cp_async16_hint(st + ch_dst[cls][m], ch_src[cls][m] + roff, pol);
-            else
-              cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
-          }
+              WB_IN(ch_dst[cls][m], 9 * SW - (E - 1)))
+            cp_async16(st + ch_dst[cls][m], ch_src[cls][m] + roff);
       }
     } else {
       const int ncols = w + 2 * kPad;
@@ -985,7 +942,6 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
         }
       }
     }
-    ++nreq;
     req_rw = (req_rw + 1 == p.ny) ? 0 : req_rw + 1;
     row_m = row_0;
     row_0 = row_p;
