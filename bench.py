@@ -448,12 +448,19 @@ def run_serving(args, stream, torch, cfg):
     b = batch(wblbe.FP64)
     srv = serve.Server(b)
     rep = srv.run(reqs, duration=0.0, drain=True, stop_after=None, time_cap=args.serve_drain_cap)
+    # requests still running at the cap: how far they got
+    unfinished = []
+    for cid, r in srv.resident.items():
+        info = b.info(cid)
+        unfinished.append({"nx": r.params.nx, "ny": r.params.ny, "tau": r.params.tau,
+                           "state": "running at the cap", "steps": info["steps"],
+                           "umax": info["stats"]["umax"]})
     b.close()
     drained = rep.summary()
     drained["requests"] = [{"nx": r.params.nx, "ny": r.params.ny, "tau": r.params.tau,
                             "state": r.state, "steps": r.steps,
                             "latency_s": None if math.isnan(r.finished) else r.finished - r.arrival}
-                           for r in sorted(rep.completed, key=lambda q: q.rid)]
+                           for r in sorted(rep.completed, key=lambda q: q.rid)] + unfinished
     drained["policy"] = (f"the first {len(reqs)} requests of the FP64 serving stream, all "
                          f"offered at t = 0, served until each stopped (cap "
                          f"{args.serve_drain_cap} s)")
@@ -669,7 +676,7 @@ def main():
     ap.add_argument("--serve-window", type=float, default=20.0)
     ap.add_argument("--serve-window-fp64", type=float, default=10.0)
     ap.add_argument("--serve-drained", type=int, default=16)
-    ap.add_argument("--serve-drain-cap", type=float, default=60.0)
+    ap.add_argument("--serve-drain-cap", type=float, default=90.0)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[50.0, 200.0, 1000.0])
     ap.add_argument("--serve-arena-gb", type=int, default=24)
