@@ -368,6 +368,49 @@ int64_t wblbe_slabs_kernel_launches(wblbe_slabs_handle h);
 wblbe_status wblbe_slabs_destroy(wblbe_slabs_handle h);
 const char* wblbe_slabs_last_error(wblbe_slabs_handle h);
 
+/* ---- three dimensions: D3Q19, FP64 ----------------------------------------
+ * The paper's construction is written for D dimensions (Eq. mFeq, Eq. mF and
+ * Eq. mFi, whose isotropic term carries D; Sec. V notes it carries over to
+ * other LBE models).  These entry points run it, and the standard scheme, on
+ * the D3Q19 lattice (D = 3, cs^2 = 1/3, weights 1/3, 1/18, 1/36) with the
+ * isotropic central stencils grad(phi) = 3 sum_i w_i c_i phi(x + c_i),
+ * lap(phi) = 6 sum_i w_i (phi(x + c_i) - phi(x)), periodic in x, y, z, in
+ * float64.  Direction order (rest, axes, edges in opposite pairs):
+ *   c0 = (0,0,0); c1..c6 = (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1);
+ *   c7..c18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *             (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
+ * Scalar fields are [nz][ny][nx] float64 (x fastest); u is [3][nz][ny][nx];
+ * populations [19][nz][ny][nx].  Conventions as for the 2D API. */
+typedef struct wblbe3_ctx* wblbe3_handle;
+
+typedef struct {
+  int32_t nx, ny, nz;              /* ny, nz <= 65535                      */
+  double tau, kappa, beta, rho_l, rho_g;
+  double rho0;                     /* Eq. mFeq; well-balanced scheme only  */
+  int32_t scheme;                  /* WBLBE_STANDARD | WBLBE_WELL_BALANCED */
+} wblbe3_params;
+
+/* Workspace bytes (0 on invalid parameters): two population buffers, the
+ * density and chemical-potential fields, staging and reduction records. */
+size_t wblbe3_workspace_bytes(const wblbe3_params* params);
+wblbe_status wblbe3_create(const wblbe3_params* params, void* dev_workspace,
+                           size_t workspace_bytes, void* cuda_stream,
+                           wblbe3_handle* out);
+/* u = 0, f = f^eq(rho, 0); rho [nz][ny][nx] on the host or device. */
+wblbe_status wblbe3_init_rho(wblbe3_handle h, const double* rho,
+                             int32_t rho_on_device);
+/* Advance nsteps steps (three kernels per step; asynchronous). */
+wblbe_status wblbe3_step(wblbe3_handle h, int64_t nsteps);
+/* rho, u ([3][nz][ny][nx]), mu (each may be NULL) and the stats of the
+ * current state.  Synchronises. */
+wblbe_status wblbe3_moments(wblbe3_handle h, double* rho, double* u, double* mu,
+                            int32_t out_on_device, wblbe_stats* stats);
+wblbe_status wblbe3_get_populations(wblbe3_handle h, double* f, int32_t on_device);
+int64_t wblbe3_step_count(wblbe3_handle h);
+int64_t wblbe3_kernel_launches(wblbe3_handle h);
+wblbe_status wblbe3_destroy(wblbe3_handle h);
+const char* wblbe3_last_error(wblbe3_handle h);
+
 /* ---- allocation-free statistics pass ------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
  * cannot allocate device memory at all: hosts whose own allocator has

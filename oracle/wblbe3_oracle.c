@@ -31,6 +31,9 @@
  *
  * Populations are stored as f[i][z][y][x] (x fastest).  Compile with
  * -ffp-contract=off: the arithmetic is exactly the order written here.
+ * Built with -DORC_DENSITY_PAIRWISE (tests only), rho = sum_i f_i is summed
+ * in pairs instead of in sequence, nothing else changed: the spread between
+ * the two builds measures the FP64 conditioning of the update.
  */
 #include <math.h>
 #include <stddef.h>
@@ -170,8 +173,13 @@ void o3_macro(const o3_params* p, const double* f, double* rho_out, double* mu_o
   double* gm = (double*)malloc(3 * n * sizeof(double));
   double* gr = (double*)malloc(3 * n * sizeof(double));
   for (size_t k = 0; k < n; ++k) {
+#ifdef ORC_DENSITY_PAIRWISE
+    double s = f[k];
+    for (int i = 1; i < Q3; i += 2) s += f[(size_t)i * n + k] + f[(size_t)(i + 1) * n + k];
+#else
     double s = 0.0;
     for (int i = 0; i < Q3; ++i) s += f[(size_t)i * n + k];
+#endif
     rho[k] = s;
   }
   o3_laplacian(p, rho, lap);

@@ -18,7 +18,7 @@ LIB_PATH = LIB_DIR / f"libwblbe_{platform.machine()}.so"
 # the same sources built with -DWBLBE_DEBUG_BOUNDS (checked accesses, a debugging aid)
 DEBUG_LIB_PATH = LIB_DIR / f"libwblbe_bounds_{platform.machine()}.so"
 SOURCES = [CSRC / "batch.cu", CSRC / "wblbe.cu", CSRC / "strip_variants.cu",
-           CSRC / "wblbe_noalloc.cu", CSRC / "probe.cu", CSRC / "slabs.cu"]
+           CSRC / "wblbe_noalloc.cu", CSRC / "probe.cu", CSRC / "slabs.cu", CSRC / "d3q19.cu"]
 DEPENDS = SOURCES + [CSRC / "lbm_kernels.cuh", CSRC / "strip_launch.cuh",
                      ROOT / "include" / "wblbe.h"]
 

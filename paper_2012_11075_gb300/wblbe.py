@@ -136,6 +136,17 @@ _SIGNATURES = {
     "wblbe_slabs_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_slabs_destroy": (ctypes.c_int, [_H]),
     "wblbe_slabs_last_error": (ctypes.c_char_p, [_H]),
+    "wblbe3_workspace_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "wblbe3_create": (ctypes.c_int, [ctypes.c_void_p, _P, ctypes.c_size_t, _P,
+                                     ctypes.POINTER(_H)]),
+    "wblbe3_init_rho": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
+    "wblbe3_step": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "wblbe3_moments": (ctypes.c_int, [_H, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(CStats)]),
+    "wblbe3_get_populations": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
+    "wblbe3_step_count": (ctypes.c_int64, [_H]),
+    "wblbe3_kernel_launches": (ctypes.c_int64, [_H]),
+    "wblbe3_destroy": (ctypes.c_int, [_H]),
+    "wblbe3_last_error": (ctypes.c_char_p, [_H]),
     "wblbe_moments_noalloc": (ctypes.c_int, [ctypes.POINTER(CParams), _P, _P, _P, _P, _P,
                                              ctypes.POINTER(CStats), _P]),
     "wblbe_noalloc_last_error": (ctypes.c_char_p, []),
@@ -593,3 +604,122 @@ class Slabs:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.wblbe_slabs_kernel_launches(self.h))
+
+
+class CParams3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("beta", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("rho_g", ctypes.c_double), ("rho0", ctypes.c_double),
+                ("scheme", ctypes.c_int32)]
+
+
+# D3Q19 direction order of the wblbe3_* entry points (rest, axes, edges in
+# opposite pairs)
+D3Q19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+         (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1),
+         (1, 0, -1), (-1, 0, 1), (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+
+
+@dataclass
+class Params3:
+    """The three-dimensional (D3Q19, FP64) problem: lattice, tau, the
+    free-energy parameters, rho0 of Eq. mFeq and the scheme."""
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    kappa: float
+    beta: float
+    rho_l: float
+    rho_g: float
+    rho0: float = 0.0
+    scheme: int = WELL_BALANCED
+
+    def c(self) -> CParams3:
+        return CParams3(self.nx, self.ny, self.nz, self.tau, self.kappa, self.beta, self.rho_l,
+                        self.rho_g, self.rho0, self.scheme)
+
+
+class Solver3:
+    """One D3Q19 lattice (FP64) on the current CUDA device (wblbe3_*)."""
+
+    def __init__(self, params: Params3, stream=None):
+        import torch
+        self._torch = torch
+        self.lib = load_library()
+        self.params = params
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._cp = params.c()
+        nbytes = int(self.lib.wblbe3_workspace_bytes(ctypes.byref(self._cp)))
+        if nbytes == 0:
+            raise WblbeError(EINVAL, "invalid parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        st = self.lib.wblbe3_create(ctypes.byref(self._cp),
+                                    ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise WblbeError(st, self.lib.wblbe3_last_error(None).decode())
+        self.h = h
+
+    def _check(self, st: int) -> int:
+        if st != OK:
+            raise WblbeError(st, self.lib.wblbe3_last_error(self.h).decode())
+        return st
+
+    @property
+    def shape(self):
+        return (self.params.nz, self.params.ny, self.params.nx)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._check(self.lib.wblbe3_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_rho(self, rho):
+        if isinstance(rho, np.ndarray):
+            rho = np.ascontiguousarray(rho, dtype=np.float64)
+            _require(rho.shape == self.shape, f"rho must have shape {self.shape}")
+            self._check(self.lib.wblbe3_init_rho(self.h, ctypes.c_void_p(rho.ctypes.data), 0))
+        else:
+            _require(rho.dtype == self._torch.float64 and rho.is_contiguous()
+                     and tuple(rho.shape) == self.shape, f"rho must be float64 {self.shape}")
+            self._check(self.lib.wblbe3_init_rho(self.h, ctypes.c_void_p(rho.data_ptr()),
+                                                 1 if rho.is_cuda else 0))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.wblbe3_step(self.h, int(n)))
+
+    def moments(self):
+        st = CStats()
+        rho, mu = np.empty(self.shape), np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        self._check(self.lib.wblbe3_moments(self.h, ctypes.c_void_p(rho.ctypes.data),
+                                            ctypes.c_void_p(u.ctypes.data),
+                                            ctypes.c_void_p(mu.ctypes.data), 0, ctypes.byref(st)))
+        return {"rho": rho, "u": u, "mu": mu}, st.as_dict()
+
+    def stats(self) -> dict:
+        st = CStats()
+        self._check(self.lib.wblbe3_moments(self.h, None, None, None, 1, ctypes.byref(st)))
+        return st.as_dict()
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((19,) + self.shape)
+        self._check(self.lib.wblbe3_get_populations(self.h, ctypes.c_void_p(f.ctypes.data), 0))
+        return f
+
+    @property
+    def steps(self) -> int:
+        return int(self.lib.wblbe3_step_count(self.h))
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(self.lib.wblbe3_kernel_launches(self.h))

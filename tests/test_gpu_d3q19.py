@@ -1,0 +1,130 @@
+"""The three-dimensional (D3Q19, FP64) path through the C ABI against the
+3D FP64 oracle: populations within 1e-12 (global norm; per direction below
+1e-12 or within 4x the oracle-to-oracle rounding spread, as for D2Q9), the
+fields and statistics, on droplets, ragged and tiny lattices (the stencils
+wrap onto the lattice itself), both schemes; and the well-balanced flat
+interface reaching the LBE-free discrete equilibrium on the GPU."""
+import numpy as np
+import pytest
+
+from oracle import equilibrium as eq
+from oracle import oracle3 as o3
+from paper_2012_11075_gb300 import wblbe
+from tests.gpu_helpers import CONDITIONING_FACTOR, PER_DIRECTION_TOL, need_gpu, per_direction_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+    wblbe.load_library()
+
+
+def _oracle_order():
+    """Index of each library direction in the oracle's direction order."""
+    cx, cy, cz = o3.lattice()[:3]
+    orc = list(zip(cx.tolist(), cy.tolist(), cz.tolist()))
+    return [orc.index(c) for c in wblbe.D3Q19]
+
+
+def _droplet(n, radius, width=4.0, rho_l=1.0, rho_g=0.1):
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - n // 2) ** 2 + (y - n // 2) ** 2 + (z - n // 2) ** 2)
+    mid, half = (rho_l + rho_g) / 2, (rho_l - rho_g) / 2
+    return mid - half * np.tanh(2 * (r - radius) / width)
+
+
+def _run_both(nx, ny, nz, rho, scheme, steps, tau=0.9, kappa=0.01, beta=None, rho_l=1.0,
+              rho_g=0.1, rho0=0.0):
+    if beta is None:
+        beta = eq.beta_for_width(kappa, 4.0, rho_l, rho_g)
+    g = wblbe.Solver3(wblbe.Params3(nx, ny, nz, tau, kappa, beta, rho_l, rho_g, rho0, scheme))
+    g.init_rho(rho)
+    g.step(steps)
+    fg = g.get_populations()
+    mg, sg = g.moments()
+    g.close()
+    p = o3.Params(nx, ny, nz, tau, kappa, beta, rho_l, rho_g, rho0, scheme)
+
+    def orc(pairwise=False):
+        o = o3.Oracle3(p, pairwise_density=pairwise)
+        f = o.init(rho)
+        o.step(f, steps)
+        return f[_oracle_order()], o
+
+    fo, o = orc()
+    f_orc_order = fo[np.argsort(_oracle_order())]      # back in the oracle's order
+    return (fg, mg, sg, fo, o.macro(f_orc_order), o.stats(f_orc_order),
+            lambda: orc(True)[0])
+
+
+def _check(fg, mg, sg, fo, mo, so, again, beta, rho_l, rho_g):
+    assert np.all(np.isfinite(fg))
+    scale = np.abs(fo).max()
+    glob = np.abs(fg - fo).max() / scale
+    assert glob < 1e-12, glob
+    per = per_direction_errors(fg, fo)
+    if max(e for e in per if e is not None) >= PER_DIRECTION_TOL:
+        spread = per_direction_errors(again(), fo)
+        for e, s in zip(per, spread):
+            if e is not None and e >= PER_DIRECTION_TOL:
+                assert e <= CONDITIONING_FACTOR * s, (per, spread)
+    assert np.abs(mg["rho"] - mo["rho"]).max() <= 1e-12 * np.abs(mo["rho"]).max()
+    assert np.abs(mg["u"] - mo["u"]).max() <= max(1e-12 * np.abs(mo["u"]).max(), 1e-15)
+    assert np.abs(mg["mu"] - mo["mu"]).max() <= 1e-12 * 2 * beta * (rho_l - rho_g) ** 3
+    assert abs(sg["mass"] - so["mass"]) <= 1e-13 * so["mass"]
+    assert sg["umax"] == pytest.approx(so["umax"], rel=1e-9, abs=1e-15)
+
+
+@pytest.mark.parametrize("scheme", [wblbe.WELL_BALANCED, wblbe.STANDARD])
+def test_d3q19_droplet_matches_oracle(scheme):
+    """16^3 droplet, R = 5, W = 4, tau = 1.0, 200 steps; density ratio 10
+    for the WB scheme, 2 for the standard one (unstable at 10, as in 2D)."""
+    n = 16
+    rho_g = 0.1 if scheme == wblbe.WELL_BALANCED else 0.5
+    rho = _droplet(n, 5.0, rho_g=rho_g)
+    beta = eq.beta_for_width(0.01, 4.0, 1.0, rho_g)
+    out = _run_both(n, n, n, rho, scheme, 200, tau=1.0, beta=beta, rho_l=1.0, rho_g=rho_g)
+    _check(*out, beta, 1.0, rho_g)
+
+
+@pytest.mark.parametrize("shape", [(3, 4, 5), (1, 1, 17), (5, 1, 3), (7, 6, 5), (17, 1, 2),
+                                   (130, 3, 2)])
+@pytest.mark.parametrize("scheme", [wblbe.WELL_BALANCED, wblbe.STANDARD])
+def test_d3q19_ragged_and_tiny_lattices(shape, scheme):
+    """Random fields; widths below and above one 128-thread block; lattices
+    narrower than the stencil in every direction."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx * 10000 + ny * 100 + nz)
+    rho = 0.6 + 0.3 * rng.uniform(-1, 1, (nz, ny, nx))
+    out = _run_both(nx, ny, nz, rho, scheme, 50, tau=0.85, kappa=0.0128, beta=0.01,
+                    rho_l=1.0, rho_g=0.2)
+    _check(*out, 0.01, 1.0, 0.2)
+
+
+def test_d3q19_rho0_is_an_offset():
+    """rho0 of Eq. mFeq only shifts the stored populations (as in 2D)."""
+    n = 10
+    rho = _droplet(n, 3.0)
+    out = _run_both(n, n, n, rho, wblbe.WELL_BALANCED, 100, tau=1.0, rho0=0.3)
+    _check(*out, eq.beta_for_width(0.01, 4.0, 1.0, 0.1), 1.0, 0.1)
+
+
+def test_d3q19_flat_interface_reaches_discrete_equilibrium():
+    """Slab along z (1 x 1 x 21): the WB scheme on the GPU relaxes to the
+    Newton solution of the 1D discrete balance mu = const."""
+    n = 21
+    zs = np.arange(n, dtype=float)
+    d = np.minimum(zs, n - zs)
+    prof = 0.55 + 0.45 * np.tanh(2 * (d - n / 4) / 4.0)
+    beta = eq.beta_for_width(0.01, 4.0, 1.0, 0.1)
+    g = wblbe.Solver3(wblbe.Params3(1, 1, n, 0.8, 0.01, beta, 1.0, 0.1, 0.0,
+                                    wblbe.WELL_BALANCED))
+    g.init_rho(prof[:, None, None].copy())
+    g.step(40000)
+    m, st = g.moments()
+    g.close()
+    rN, _ = eq.discrete_flat_equilibrium(prof, 0.01, beta, 1.0, 0.1)
+    assert np.max(np.abs(m["rho"][:, 0, 0] - rN)) < 1e-10
+    assert st["umax"] < 1e-13 and st["mu_max"] - st["mu_min"] < 1e-13
