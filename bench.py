@@ -44,8 +44,8 @@ BYTES_PER_LU = {"f32": 72, "f64": 144}          # 9 reads + 9 writes per node up
 SUBSTEPS = {"f32": 200, "f64": 40}              # lattice steps per benchmark step
 # FP64 flops per lattice update of the FP64 step kernel, from the ncu
 # instruction mix (2 x DFMA + DADD + DMUL per node, halo work included;
-# 2048^2 well-balanced case: DADD 45.6, DMUL 24.2, DFMA 48.5)
-FP64_FLOPS_PER_LU = 166.8
+# 2048^2 well-balanced case: DADD 41.5, DMUL 21.2, DFMA 48.75)
+FP64_FLOPS_PER_LU = 160.3
 # oldest state (lattice steps since initialisation) a timed step may start
 # from; see time_device
 MAX_STATE_AGE = 1200

@@ -121,6 +121,19 @@ __device__ __forceinline__ T chem_pot(T c, T e, T w, T n, T s, T ne, T nw, T se,
   return mu0 - kappa6 * lap6;
 }
 
+// chem_pot with the row sums ew = e + w, nenw = ne + nw and sesw = se + sw
+// passed in (the FP64 strip kernel forms each row's sum once and carries it
+// to the two rows above): the same operations in the same order, so the
+// same result.
+template <typename T>
+__device__ __forceinline__ T chem_pot_rows(T c, T ew, T n, T s, T nenw, T sesw, T two_beta,
+                                           T dl, T dg, T kappa6) {
+  T a = c + dl, b = c + dg;
+  T mu0 = two_beta * a * b * (a + b);
+  T lap6 = T(4) * (ew + (n + s)) + (nenw + sesw) - T(20) * c;
+  return mu0 - kappa6 * lap6;
+}
+
 // 1/x: the hardware reciprocal approximation in FP32 (about 1 ulp; the FP32
 // path's error budget is set by float storage anyway).
 __device__ __forceinline__ float recip(float x) {
@@ -164,9 +177,11 @@ __device__ __forceinline__ double recip(double x) {
 template <typename T>
 struct CollideConsts {
   T omega, kf, keep, kf_m3, rho_ref, kappa, kf12;
+  T kfm12, kf36, kf432;             // -kforce/12, kforce/36, kforce/432 (collide_wb12)
   __device__ explicit CollideConsts(const KParams& p)
       : kf(T(p.kforce)), kf_m3(T(-3.0 * p.kforce)), rho_ref(T(p.rho_ref)), kappa(T(p.kappa)),
-        kf12(T(p.kforce / 12.0)) {
+        kf12(T(p.kforce / 12.0)), kfm12(T(-p.kforce / 12.0)), kf36(T(p.kforce / 36.0)),
+        kf432(T(p.kforce / 432.0)) {
     const T w = T(p.omega);
     if (w >= T(0.5)) {
       omega = w;
@@ -201,6 +216,70 @@ template <typename T>
 __device__ __forceinline__ void textbook_pairs(T (&g)[9], T rs, T rho, T ux, T uy, T Fx,
                                                T Fy, const CollideConsts<T>& q);
 
+// The well-balanced collision from 12 grad mu and 12 grad rho (iso_grad12),
+// the same terms as collide below arranged for fewer operations, which is
+// what bounds the FP64 path.  F = -rho grad mu enters the update only as F/2
+// (the velocity, Eq. rhoU) and as kforce F, so both are formed from the
+// gradient directly; G = F + cs^2 grad rho enters only as kforce G; and t,
+// k_u are carried divided by 36, so that the even parts are
+// E_dg = t' + 2 k_u', E_ax = 3 t' + E_dg and E_0 = 16 (t' - k_u') + omega b_0.
+template <typename T>
+__device__ __forceinline__ void collide_wb12(T (&g)[9], T rs, T gmx, T gmy, T grx, T gry,
+                                             const CollideConsts<T>& q, T& ux_out,
+                                             T& uy_out) {
+  constexpr bool kShifted = sizeof(T) == 4;
+  const T omega = q.omega;
+  const T rho = kShifted ? rs + q.rho_ref : rs;
+  const T hm = rho * T(-1.0 / 24.0);                   // F/2 = hm (12 grad mu)
+  const T kcm = rho * q.kfm12;                         // kforce F = kcm (12 grad mu)
+  const T d13 = g[1] - g[3], d24 = g[2] - g[4], d57 = g[5] - g[7], d86 = g[8] - g[6];
+  const T jx = (d13 + d57) + d86;
+  const T jy = (d24 + d57) - d86;
+  const T inv_rho = recip(rho);
+  const T ux = (jx + hm * gmx) * inv_rho;               // Eq. rhoU
+  const T uy = (jy + hm * gmy) * inv_rho;
+  ux_out = ux;
+  uy_out = uy;
+  const T kFx = kcm * gmx, kFy = kcm * gmy;
+  const T kGx = kFx + q.kf36 * grx, kGy = kFy + q.kf36 * gry;
+  const T orho = omega * rho;
+  const T uu = ux * ux + uy * uy;
+  const T uK = ux * kGx + uy * kGy;                     // kforce u.G
+  const T tq = (orho * T(-1.0 / 24.0)) * uu - T(1.0 / 12.0) * uK;   // t / 36
+  const T kq = q.kf432 * (ux * grx + uy * gry);         // k_u / 36
+  const T Cdg = tq + T(2) * kq;
+  const T Cax = T(3) * tq + Cdg;
+  const T E0 = T(16) * (tq - kq) + omega * rs;          // b_0 = rs, b_ax = b_dg = 0
+  const T hrho = T(0.5) * orho;
+  const T Mx = orho * ux + kFx;                         // odd parts: omega rho c.u + kforce c.F
+  const T My = orho * uy + kFy;
+  const T E1 = Cax + ux * (hrho * ux + kGx);            // pair (1,3): c = (1,0)
+  const T O1 = T(1.0 / 3.0) * Mx;
+  const T E2 = Cax + uy * (hrho * uy + kGy);            // pair (2,4): c = (0,1)
+  const T O2 = T(1.0 / 3.0) * My;
+  const T cu5 = ux + uy;                                // pair (5,7): c = (1,1)
+  const T E5 = Cdg + (T(0.25) * cu5) * (hrho * cu5 + (kGx + kGy));
+  const T O5 = T(1.0 / 12.0) * (Mx + My);
+  const T cu6 = uy - ux;                                // pair (6,8): c = (-1,1)
+  const T E6 = Cdg + (T(0.25) * cu6) * (hrho * cu6 + (kGy - kGx));
+  const T O6 = T(1.0 / 12.0) * (My - Mx);
+  const T keep = q.keep;
+  g[1] = keep * g[1] + (E1 + O1);
+  g[3] = keep * g[3] + (E1 - O1);
+  g[2] = keep * g[2] + (E2 + O2);
+  g[4] = keep * g[4] + (E2 - O2);
+  g[5] = keep * g[5] + (E5 + O5);
+  g[7] = keep * g[7] + (E5 - O5);
+  g[6] = keep * g[6] + (E6 + O6);
+  g[8] = keep * g[8] + (E6 - O6);
+  if (kShifted) {
+    (void)E0;                                           // mass balance, as in collide
+    g[0] = rs - (((g[1] + g[3]) + (g[2] + g[4])) + ((g[5] + g[7]) + (g[6] + g[8])));
+  } else {
+    g[0] = keep * g[0] + E0;
+  }
+}
+
 // GS: the gradient inputs are GS times the gradients (12: the strip kernel
 // passes 12 grad, see iso_grad12, and the factor 1/12 is folded into the
 // few places that use them; 1: plain gradients).
@@ -212,6 +291,10 @@ __device__ __forceinline__ void collide(T (&g)[9], T rs, T gmx, T gmy, T grx,
   constexpr bool kShifted = sizeof(T) == 4;   // FP32 storage is always shifted
   constexpr bool kG12 = GS == 12;
   static_assert(GS == 1 || GS == 12, "gradient scale");
+  if constexpr (WB && kG12) {
+    collide_wb12<T>(g, rs, gmx, gmy, grx, gry, q, ux_out, uy_out);
+    return;
+  }
   const T omega = q.omega, kf = q.kf;
   // FP64 storage is unshifted (rho_ref = 0)
   const T rho = kShifted ? rs + q.rho_ref : rs;
@@ -378,6 +461,17 @@ __device__ __forceinline__ void iso_grad12(T e, T w, T n, T s, T ne, T nw, T se,
   const T d1 = ne - sw, d2 = se - nw;
   gx = T(4) * (e - w) + (d1 + d2);
   gy = T(4) * (n - s) + (d1 - d2);
+}
+
+// iso_grad12 from per-row x-differences q = f(x+1) - f(x-1) and x-sums
+// p = f(x+1) + f(x-1) of the rows above (n), at (c) and below (s), which
+// the FP64 strip kernel forms once per row and carries:
+// 12 df/dx = 4 q_c + (q_n + q_s),  12 df/dy = 4 (n - s) + (p_n - p_s).
+template <typename T>
+__device__ __forceinline__ void iso_grad12_rows(T qc, T qn, T qs, T n, T s, T pn, T ps, T& gx,
+                                                T& gy) {
+  gx = T(4) * qc + (qn + qs);
+  gy = T(4) * (n - s) + (pn - ps);
 }
 
 // ---- packed FP32 pairs ------------------------------------------------------
@@ -987,6 +1081,10 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
   constexpr bool kPacked = sizeof(T) == 4 && R == 2;
   // rho and grad rho of the last mu row(s) of the previous iteration
   T prs = T(0), pgx = T(0), pgy = T(0);
+  // x-neighbour density sums of the own column in the rows below the
+  // density front (scalar path: rows n0-1 and n0-2)
+  T psum_c = T(0), psum_b = T(0);
+  T pdif_c = T(0), pdif_b = T(0);          // ... and x-differences (grad rho)
   float2 prs2 = make_float2(0.f, 0.f), pgx2 = prs2, pgy2 = prs2;
   const float2 tb2 = make_float2((float)ring_tb, (float)ring_tb);
   const float2 dl2 = make_float2((float)dl, (float)dl), dg2 = make_float2((float)dg, (float)dg);
@@ -1101,8 +1199,12 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 #pragma unroll
           for (int j = 0; j < R; ++j) {
             frs[j] = fgx[j] = fgy[j] = T(0);
+            const T* rn = rho_s + WB_SLOT(j, kRing) * SW;         // row above (y+1)
+            // x-neighbour sum and difference of the density row just
+            // reduced, carried to the mu rows of the next two iterations
+            const T psum_n = own ? rn[sx + 1] + rn[sx - 1] : T(0);
+            const T pdif_n = (own && !kPress) ? rn[sx + 1] - rn[sx - 1] : T(0);
             if (kfirst + n0 - 1 + j >= y0 - 1) {
-              const T* rn = rho_s + WB_SLOT(j, kRing) * SW;       // row above (y+1)
               const T* rc = rho_s + WB_SLOT(j - 1, kRing) * SW;
               const T* rsb = rho_s + WB_SLOT(j - 2, kRing) * SW;  // row below (y-1)
               T* mrow = mu_s + WB_SLOT(j - 1, kMuRing) * SW;
@@ -1111,20 +1213,26 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
                                    rn[s - 1], rsb[s + 1], rsb[s - 1], ring_tb, dl, dg, ring_k6);
               };
               if (own) {
-                mrow[sx] = at(sx);
+                mrow[sx] = chem_pot_rows<T>(rc[sx], psum_c, rn[sx], rsb[sx], psum_n, psum_b,
+                                            ring_tb, dl, dg, ring_k6);
                 frs[j] = rc[sx];
                 // 12 grad(rho) (or 12 grad(cs^2 rho - p_0)): see iso_grad12
+                // and iso_grad12_rows
                 if (kPress)
                   iso_grad12<T>(press_a(rc[sx + 1]), press_a(rc[sx - 1]), press_a(rn[sx]),
                                 press_a(rsb[sx]), press_a(rn[sx + 1]), press_a(rn[sx - 1]),
                                 press_a(rsb[sx + 1]), press_a(rsb[sx - 1]), fgx[j], fgy[j]);
                 else
-                  iso_grad12<T>(rc[sx + 1], rc[sx - 1], rn[sx], rsb[sx], rn[sx + 1], rn[sx - 1],
-                                rsb[sx + 1], rsb[sx - 1], fgx[j], fgy[j]);
+                  iso_grad12_rows<T>(pdif_c, pdif_n, pdif_b, rn[sx], rsb[sx], psum_n, psum_b,
+                                     fgx[j], fgy[j]);
               }
               if (tx == mu_lo) mrow[3] = at(3);
               if (tx == mu_hi && WB_IN(w + 4, SW)) mrow[w + 4] = at(w + 4);
             }
+            psum_b = psum_c;
+            psum_c = psum_n;
+            pdif_b = pdif_c;
+            pdif_c = pdif_n;
           }
         }
         __syncthreads();                   // barrier C
