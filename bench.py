@@ -46,6 +46,10 @@ SUBSTEPS = {"f32": 200, "f64": 40}              # lattice steps per benchmark st
 # instruction mix (2 x DFMA + DADD + DMUL per node, halo work included;
 # 2048^2 well-balanced case: DADD 41.5, DMUL 21.2, DFMA 48.75)
 FP64_FLOPS_PER_LU = 160.3
+# FP64 flops per lattice update of the three D3Q19 kernels (density 19 DADD;
+# chemical potential 39 DADD + 4 DMUL + 2 DFMA; collide 80 DADD + 43 DMUL +
+# 93 DFMA; ncu op mix on a 128^3 droplet, one thread per node, no halo work)
+D3_FLOPS_PER_LU = 375.0
 # oldest state (lattice steps since initialisation) a timed step may start
 # from; see time_device
 MAX_STATE_AGE = 1200
@@ -508,7 +512,7 @@ def run_schemes(args, stream, torch):
     return out
 
 
-def run_d3q19(args, stream, torch):
+def run_d3q19(args, stream, torch, fp64_peak=None):
     """The three-dimensional (D3Q19, FP64) well-balanced path: a periodic
     n^3 lattice with one droplet of radius n/4 (rho_l = 1, rho_g = 0.1,
     kappa = 0.01, W = 4, tau = 1.0); K benchmark steps of S lattice steps,
@@ -543,11 +547,19 @@ def run_d3q19(args, stream, torch):
     s.close()
     lups = n ** 3 * S * K / dt
     peak = measured_peaks().get("hbm_gbs") or 6800.0
+    if fp64_peak is None:
+        fp64_peak = measure_fp64_peak(stream, torch)
+    alu = lups * D3_FLOPS_PER_LU / 1e12
     return {"workload": f"d3q19_{n}^3_droplet_wb_fp64", "value": lups / 1e6, "unit": UNIT,
             "lattice_steps": S * K, "seconds": dt, "gpu_launches": launches,
             "bytes_per_lattice_update": 304,
             "hbm_frac_algorithmic": 304 * lups / 1e9 / peak,
             "hbm_frac_moved": 496 * lups / 1e9 / peak,
+            # the three kernels are bound by the FP64 pipe (83-87 % busy)
+            "roofline_alu": {"bound": "alu", "achieved": alu, "peak": fp64_peak["tflops"],
+                             "unit": "TFLOP/s", "frac": alu / fp64_peak["tflops"],
+                             "flops_per_lattice_update": D3_FLOPS_PER_LU,
+                             "peak_source": "of measured (FP64 FMA probe kernel, this run)"},
             "umax": st["umax"], "mass_drift_rel": st["mass_drift_rel"],
             "nonfinite": bool(st["nonfinite"])}
 
@@ -688,7 +700,7 @@ def run_ours(args, world, rank, local):
     if not args.no_schemes:
         line["schemes"] = run_schemes(args, stream, torch)
     if not args.no_d3q19:
-        line["d3q19"] = run_d3q19(args, stream, torch)
+        line["d3q19"] = run_d3q19(args, stream, torch, fp64_peak)
     if not args.no_batched:
         line["batched"] = run_batched(args, stream, torch)
         if not args.no_serving:

@@ -217,15 +217,17 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
 }
 
 // Initial state of one case in the ghost layout: P_i(x) = f_i^eq(rho(x+c_i), 0)
-// - s_i at storage offset x + 4, for every stored column (ghosts included).
+// - s_i at storage offset x + ghost_off, for every stored column x = -4 ..
+// nx + 3 (ghosts included).
 template <typename T>
 __global__ void batch_init_kernel(const double* __restrict__ rho, T* __restrict__ dst,
                                   int nx, int ny, int pitch, long long plane, int wb,
                                   double rho0, LayoutParams lp) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;   // storage column
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;   // column k - 4
   const int y = blockIdx.y;
-  if (o >= nx + 2 * kPad) return;
-  const int x = wrap_index(o - kPad, nx);
+  if (k >= nx + 2 * kPad) return;
+  const int x = wrap_index(k - kPad, nx);
+  const int o = k - kPad + ghost_off<T>();                // storage column
   const double w[9] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0, 1.0 / 9.0,
                        1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 #pragma unroll
@@ -245,7 +247,8 @@ __global__ void batch_get_pops_kernel(const T* __restrict__ src, double* __restr
   const int y = blockIdx.y;
   if (x >= nx) return;
   const int sy = wrap_index(y - kCy[dir], ny);
-  const double v = (double)src[dir * plane + (long long)sy * pitch + (x - kCx[dir] + kPad)];
+  const double v =
+      (double)src[dir * plane + (long long)sy * pitch + (x - kCx[dir] + ghost_off<T>())];
   f[(size_t)y * nx + x] = v + lp.shift[dir];
 }
 
@@ -352,7 +355,9 @@ Control control_layout(int max_cases, int max_tiles, long long max_case_nodes) {
 
 int case_pitch(int nx, size_t elem) {
   const int align_elems = (int)(128 / elem);
-  return (nx + 12 + align_elems - 1) / align_elems * align_elems;   // ghosts + chunk overrun
+  const int off = elem == 4 ? ghost_off<float>() : ghost_off<double>();
+  // leading offset, right ghosts and chunk overrun
+  return (nx + off + 8 + align_elems - 1) / align_elems * align_elems;
 }
 
 size_t case_bytes(const wblbe_params* p, size_t elem) {

@@ -805,6 +805,19 @@ template <> struct Staging<double> {
 
 constexpr int kPad = 4;   // staged columns on each side of a strip (x0-4 .. x0+TX+3)
 
+// Storage offset of column x in the ghost layout of the batched kernel
+// (column x at x + ghost_off, its four ghost columns on each side at
+// ghost_off - 4 .. ghost_off - 1 and nx + ghost_off .. nx + ghost_off + 3):
+// 4, so that a strip's columns and both its halos span the fewest 64-byte
+// pieces of a row (9 for 128 float columns).  An offset of 32 floats, which
+// makes every warp's 32 stores fill whole 128-byte lines, moved 18 % more
+// DRAM reads (the halos then straddle one more piece on each side) and did
+// not change the writes.
+template <typename T>
+__host__ __device__ constexpr int ghost_off() {
+  return 4;
+}
+
 __host__ __device__ constexpr size_t strip_smem_bytes(int tile, int stages, size_t elem) {
   // 128 bytes of alignment slack + the buffers
   return 128 + ((size_t)stages * 9 + kRing + kMuRing) * (size_t)(tile + 2 * kPad) * elem;
@@ -902,13 +915,15 @@ __device__ __forceinline__ void emit_node(const KParams& p, const MomentsOut& mo
 }
 
 // GHOST selects the row layout with ghost columns used by the batched
-// kernel: column x of a row is stored at x + 4 and the four columns on each
-// side hold copies of the wrapped columns (x = -4..-1 -> nx-4..nx-1,
-// x = nx..nx+3 -> 0..3), refreshed by every store of a boundary column.  A
+// kernel: column x of a row is stored at x + ghost_off<T>() and the four
+// columns on each side hold copies of the wrapped columns (x = -4..-1 ->
+// nx-4..nx-1, x = nx..nx+3 -> 0..3), refreshed by every store of a boundary
+// column.  A
 // strip then reads one contiguous range per plane row, always in 16-byte
 // chunks through L2 (cp.async.cg), whatever its width: needed when one
 // kernel launch reads data that other CTAs wrote during the same launch (L1
-// is not coherent across SMs).  Requires nx >= 8 and pitch >= nx + 12.
+// is not coherent across SMs).  Requires nx >= 8 and
+// pitch >= nx + ghost_off + 8.
 // Offsets within a plane are 32-bit: pitch * ny < 2^31 (checked by the host).
 template <typename T, int SCH, int MODE, int TX, bool GHOST = false>
 __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restrict__ dst,
@@ -991,7 +1006,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
       const int i = class_plane(cls, a);
       int col = x0 - kPad + j * E;
       if (GHOST) {
-        col += kPad;                       // storage offset of column x is x + 4
+        col += ghost_off<T>();             // storage offset of column x
       } else {
         if (col < 0) col += p.nx;
         else if (col >= p.nx) col -= p.nx;
@@ -1052,7 +1067,7 @@ __device__ __forceinline__ void strip_pass(const T* __restrict__ src, T* __restr
 
   // store position of column x0 + tx within a plane; ghost copies a boundary
   // column also writes: x < 4 -> +nx (right ghost), x >= nx - 4 -> -nx (left)
-  const int xcol = x0 + tx + (GHOST ? kPad : 0);
+  const int xcol = x0 + tx + (GHOST ? ghost_off<T>() : 0);
   const int xg = x0 + tx;
   const bool ghost_r = GHOST && own && xg < kPad;
   const bool ghost_l = GHOST && own && xg >= p.nx - kPad;
