@@ -111,9 +111,11 @@ __global__ void __launch_bounds__(kBlock3) d3_chem_pot(const double* __restrict_
   mu[at3(p, x, y, z)] = p.two_beta * a * b * (a + b) - p.kappa * lap;
 }
 
-// 3 sum_i w_i c_i phi(x + c_i): (axis differences)/6 + (edge differences)/12.
-__device__ __forceinline__ void grad3(const double* __restrict__ phi, const P3& p, int x,
-                                      int y, int z, double& gx, double& gy, double& gz) {
+// 12 grad(phi) = 36 sum_i w_i c_i phi(x + c_i): 2 (axis differences) +
+// (edge differences); the factor 1/12 is folded into the constants that
+// use the gradients.
+__device__ __forceinline__ void grad3x12(const double* __restrict__ phi, const P3& p, int x,
+                                         int y, int z, double& gx, double& gy, double& gz) {
   auto v = [&](int dx, int dy, int dz) {
     return __ldg(phi + at3(p, wrap3(x + dx, p.nx), wrap3(y + dy, p.ny), wrap3(z + dz, p.nz)));
   };
@@ -122,9 +124,9 @@ __device__ __forceinline__ void grad3(const double* __restrict__ phi, const P3& 
   const double exy1 = v(1, 1, 0) - v(-1, -1, 0), exy2 = v(1, -1, 0) - v(-1, 1, 0);
   const double exz1 = v(1, 0, 1) - v(-1, 0, -1), exz2 = v(1, 0, -1) - v(-1, 0, 1);
   const double eyz1 = v(0, 1, 1) - v(0, -1, -1), eyz2 = v(0, 1, -1) - v(0, -1, 1);
-  gx = (1.0 / 6.0) * axx + (1.0 / 12.0) * ((exy1 + exy2) + (exz1 + exz2));
-  gy = (1.0 / 6.0) * axy + (1.0 / 12.0) * ((exy1 - exy2) + (eyz1 + eyz2));
-  gz = (1.0 / 6.0) * axz + (1.0 / 12.0) * ((exz1 - exz2) + (eyz1 - eyz2));
+  gx = 2.0 * axx + ((exy1 + exy2) + (exz1 + exz2));
+  gy = 2.0 * axy + ((exy1 - exy2) + (eyz1 + eyz2));
+  gz = 2.0 * axz + ((exz1 - exz2) + (eyz1 - eyz2));
 }
 
 // The collision of one node, and its stores (MOMENTS: fields and stats
@@ -154,26 +156,31 @@ __global__ void __launch_bounds__(kBlock3) d3_collide(const double* __restrict__
                                    wrap3(z - cz3(i), p.nz))];
     const long long k = at3(p, x, y, z);
     const double r = rho[k];
+    // 12 grad mu, 12 grad rho; F = -rho grad mu (Eq. mF), or the potential
+    // form cs^2 grad rho - rho grad mu of the standard scheme
     double gmx, gmy, gmz, grx, gry, grz;
-    grad3(mu, p, x, y, z, gmx, gmy, gmz);
-    grad3(rho, p, x, y, z, grx, gry, grz);
+    grad3x12(mu, p, x, y, z, gmx, gmy, gmz);
+    grad3x12(rho, p, x, y, z, grx, gry, grz);
+    const double nr = r * (-1.0 / 12.0);
     double Fx, Fy, Fz;
     if (WB) {
-      Fx = -r * gmx;                                            // Eq. mF
-      Fy = -r * gmy;
-      Fz = -r * gmz;
+      Fx = nr * gmx;
+      Fy = nr * gmy;
+      Fz = nr * gmz;
     } else {
-      Fx = (1.0 / 3.0) * grx - r * gmx;                         // potential form
-      Fy = (1.0 / 3.0) * gry - r * gmy;
-      Fz = (1.0 / 3.0) * grz - r * gmz;
+      Fx = (1.0 / 36.0) * grx + nr * gmx;
+      Fy = (1.0 / 36.0) * gry + nr * gmy;
+      Fz = (1.0 / 36.0) * grz + nr * gmz;
     }
-    const double jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) +
-                      (g[13] - g[14]);
-    const double jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) +
-                      (g[17] - g[18]);
-    const double jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) +
-                      (g[18] - g[17]);
-    const double inv = 1.0 / r;
+    // momentum from the differences of opposite pairs (each edge difference
+    // serves two components)
+    const double d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
+    const double d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
+    const double d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
+    const double jx = ((d12 + d78) + (d910 + d1112)) + d1314;
+    const double jy = ((d34 + d78) - (d910 - d1516)) + d1718;
+    const double jz = ((d56 + d1112) - (d1314 - d1516)) - d1718;
+    const double inv = recip(r);
     const double ux = (jx + 0.5 * Fx) * inv, uy = (jy + 0.5 * Fy) * inv,
                  uz = (jz + 0.5 * Fz) * inv;                     // Eq. rhoU
     const double muc = mu[k];
@@ -195,38 +202,48 @@ __global__ void __launch_bounds__(kBlock3) d3_collide(const double* __restrict__
       const double keep = 1.0 - om;
       double Gx = Fx, Gy = Fy, Gz = Fz;
       if (WB) {
-        Gx = Fx + (1.0 / 3.0) * grx;
-        Gy = Fy + (1.0 / 3.0) * gry;
-        Gz = Fz + (1.0 / 3.0) * grz;
+        Gx = Fx + (1.0 / 36.0) * grx;                           // G = F + cs^2 grad rho
+        Gy = Fy + (1.0 / 36.0) * gry;
+        Gz = Fz + (1.0 / 36.0) * grz;
       }
       const double orho = om * r;
       const double t = -1.5 * orho * (ux * ux + uy * uy + uz * uz) -
                        3.0 * kf * (ux * Gx + uy * Gy + uz * Gz);
-      const double ku = WB ? kf * (ux * grx + uy * gry + uz * grz) : 0.0;
-      const double base = WB ? 0.0 : orho;                     // standard: omega rho w
-      const double Mx = orho * ux + kf * Fx, My = orho * uy + kf * Fy, Mz = orho * uz + kf * Fz;
-      const double h9 = 4.5 * orho;
-      // pair with lattice vector (a, b, c), weight w, h = (3|c|^2 - 3)/2
-      auto pair = [&](int i, int j, double w, double h, double cu, double cG, double cM) {
-        const double E = w * (t + base + cu * (h9 * cu + 9.0 * kf * cG) + h * ku);
-        const double O = 3.0 * w * cM;
-        g[i] = keep * g[i] + (E + O);
-        g[j] = keep * g[j] + (E - O);
+      const double ku = WB ? (kf * (1.0 / 12.0)) * (ux * grx + uy * gry + uz * grz) : 0.0;
+      // per-node constants of the pairs, with the weights folded in
+      // (w_ax = 1/18, w_edge = 1/36): E = C + cu (A cu + K.c), O = 3 w c.M
+      const double Ca = WB ? (1.0 / 18.0) * t : (1.0 / 18.0) * (t + orho);
+      const double Ce = WB ? (1.0 / 36.0) * (t + 1.5 * ku) : (1.0 / 36.0) * (t + orho);
+      const double Aa = 0.25 * orho, Ae = 0.125 * orho;          // w 9/2 omega rho
+      const double kh = 0.5 * kf, kq = 0.25 * kf, k6 = kf * (1.0 / 6.0);
+      const double Kax = kh * Gx, Kay = kh * Gy, Kaz = kh * Gz;  // 9 w_ax kforce G
+      const double Kex = kq * Gx, Key = kq * Gy, Kez = kq * Gz;  // 9 w_edge kforce G
+      const double o6 = orho * (1.0 / 6.0);                      // 3 w_ax (omega rho u + kforce F)
+      const double Mx = o6 * ux + k6 * Fx, My = o6 * uy + k6 * Fy, Mz = o6 * uz + k6 * Fz;
+      auto axis = [&](int i, int j, double cu, double K, double M) {
+        const double E = Ca + cu * (Aa * cu + K);
+        g[i] = keep * g[i] + (E + M);
+        g[j] = keep * g[j] + (E - M);
       };
-      constexpr double wa = 1.0 / 18.0, we = 1.0 / 36.0;
-      pair(1, 2, wa, 0.0, ux, Gx, Mx);
-      pair(3, 4, wa, 0.0, uy, Gy, My);
-      pair(5, 6, wa, 0.0, uz, Gz, Mz);
-      pair(7, 8, we, 1.5, ux + uy, Gx + Gy, Mx + My);
-      pair(9, 10, we, 1.5, ux - uy, Gx - Gy, Mx - My);
-      pair(11, 12, we, 1.5, ux + uz, Gx + Gz, Mx + Mz);
-      pair(13, 14, we, 1.5, ux - uz, Gx - Gz, Mx - Mz);
-      pair(15, 16, we, 1.5, uy + uz, Gy + Gz, My + Mz);
-      pair(17, 18, we, 1.5, uy - uz, Gy - Gz, My - Mz);
+      // edge pair: 3 w_edge c.M = (Ma + Mb) / 2 for c = a + b
+      auto edge = [&](int i, int j, double cu, double K, double S) {
+        const double E = Ce + cu * (Ae * cu + K);
+        g[i] = keep * g[i] + (E + 0.5 * S);
+        g[j] = keep * g[j] + (E - 0.5 * S);
+      };
+      axis(1, 2, ux, Kax, Mx);
+      axis(3, 4, uy, Kay, My);
+      axis(5, 6, uz, Kaz, Mz);
+      edge(7, 8, ux + uy, Kex + Key, Mx + My);
+      edge(9, 10, ux - uy, Kex - Key, Mx - My);
+      edge(11, 12, ux + uz, Kex + Kez, Mx + Mz);
+      edge(13, 14, ux - uz, Kex - Kez, Mx - Mz);
+      edge(15, 16, uy + uz, Key + Kez, My + Mz);
+      edge(17, 18, uy - uz, Key - Kez, My - Mz);
       // rest: WB f_0^eq - s_0 = rho - w_0 3/2 rho u.u, F_0 = w_0 (-3 u.G - 3/2 u.grad rho);
       // standard f_0^eq = w_0 rho (1 - 3/2 u.u), F_0 = w_0 (-3 u.G)
       const double w0 = 1.0 / 3.0;
-      g[0] = keep * g[0] + (WB ? om * r + w0 * (t - 1.5 * ku) : w0 * (t + orho));
+      g[0] = keep * g[0] + (WB ? orho + w0 * (t - 1.5 * ku) : w0 * (t + orho));
 #pragma unroll
       for (int i = 0; i < kQ3; ++i) dst[i * p.plane + k] = g[i];
     }
