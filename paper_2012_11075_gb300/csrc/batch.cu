@@ -44,6 +44,7 @@ using namespace wblbe;
 namespace {
 
 constexpr int kMaxNb = 12;               // neighbour tiles a tile may wait on
+static_assert(kMaxNb + 1 <= 32, "one lane of warp 0 per awaited counter");
 constexpr int kHaloReach = 3;            // nodes a step reads around its tile
 constexpr size_t kAlignB = 256;
 constexpr long long kDefaultSpins = 1LL << 22;   // x ~64 ns sleep: about 0.3 s
@@ -105,13 +106,15 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
     if (item >= total) break;
     const int j = item / ntiles, t = item - j * ntiles;
     const TileDev tile = d.tiles[t];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // warp 0 waits for the tile itself (its step j-1 may run on another
+      // CTA) and for every neighbour its halo reads, one counter per lane,
+      // so that the waits overlap
+      const int lane = threadIdx.x;
       int ok = ld_acquire(d.status) == 0;
-      // wait for the tile itself (its step j-1 may run on another CTA), then
-      // for every neighbour its halo reads
-      for (int q = -1; q < kMaxNb && ok && j > 0; ++q) {
-        const int nb = q < 0 ? t : tile.nb[q];
-        if (nb < 0) break;
+      const int nb =
+          j == 0 ? -1 : (lane == 0 ? t : (lane <= kMaxNb ? d.tiles[t].nb[lane - 1] : -1));
+      if (ok && nb >= 0) {
         long long n = 0;
         while (ld_acquire(d.done + nb) < j) {
           if (++n > d.spins || (n % 256 == 0 && ld_acquire(d.status) != 0)) {
@@ -121,8 +124,11 @@ __global__ void __launch_bounds__(TX, Staging<T>::min_blocks_batch(TX))
           __nanosleep(64);
         }
       }
-      if (!ok) atomicOr(d.status, 1);
-      s_ok = ok;
+      ok = __all_sync(0xffffffffu, ok);
+      if (lane == 0) {
+        if (!ok) atomicOr(d.status, 1);
+        s_ok = ok;
+      }
     }
     __syncthreads();
     if (!s_ok) break;                      // nothing of this CTA is in flight
@@ -307,6 +313,7 @@ struct wblbe_batch {
   bool tiles_dirty = true;
   int ntiles = 0, nrun = 0;
   std::vector<RunCase> run_host;
+  std::vector<CaseDev> case_host;         // staging of the case table upload
   int64_t launches = 0;
   char err[256] = "";
 };
@@ -545,17 +552,21 @@ wblbe_status rebuild_tiles(wblbe_batch* b) {
   if (!b->run_host.empty())
     BCU(b, cudaMemcpyAsync(b->d_run, b->run_host.data(), b->run_host.size() * sizeof(RunCase),
                            cudaMemcpyHostToDevice, b->stream));
-  // the case table carries rows_per_tile (moments) and the buffer parity
+  // the case table carries rows_per_tile (moments) and the buffer parity:
+  // one copy of the whole table (entries of unused slots are never read)
+  b->case_host.assign(b->cases.size(), CaseDev{});
   for (size_t ci = 0; ci < b->cases.size(); ++ci) {
     const auto& c = b->cases[ci];
     if (!c.used) continue;
-    CaseDev cd{};
+    CaseDev& cd = b->case_host[ci];
     cd.kp = case_kparams(c, b->cfg.rows_per_tile);
     cd.off[0] = (long long)(c.off / b->elem);
     cd.off[1] = (long long)((c.off + c.bytes / 2) / b->elem);
     cd.cur = c.cur;
-    BCU(b, cudaMemcpyAsync(b->d_cases + ci, &cd, sizeof(cd), cudaMemcpyHostToDevice, b->stream));
   }
+  if (!b->case_host.empty())
+    BCU(b, cudaMemcpyAsync(b->d_cases, b->case_host.data(), b->case_host.size() * sizeof(CaseDev),
+                           cudaMemcpyHostToDevice, b->stream));
   // the host buffers above must stay valid until the copies ran
   BCU(b, cudaStreamSynchronize(b->stream));
   b->tiles_dirty = false;
