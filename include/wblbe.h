@@ -204,6 +204,32 @@ int64_t wblbe_kernel_launches(wblbe_handle h);
  * NULL handle or a negative step. */
 wblbe_status wblbe_set_step_count(wblbe_handle h, int64_t step);
 
+/* Bytes of device scratch that wblbe_run_sequence needs for these params:
+ * two input and two output float64 density fields plus four statistics
+ * records.  0 for NULL or non-positive sizes. */
+size_t wblbe_sequence_scratch_bytes(const wblbe_params* params);
+
+/* Relax n independent initial states one after another with the host
+ * copies overlapped: for each k, as wblbe_init_rho(rho_in[k], host), then
+ * wblbe_step(nsteps), then wblbe_moments into rho_out[k] (host) and
+ * stats[k] (may be NULL): the same results, bit for bit, as those calls
+ * made one state at a time (Eq. D2Q9 from f = f^eq(rho, 0), Eq. rhoU).
+ * State k + 1's density is copied in on a second stream while state k is
+ * computed, and state k's density and statistics are copied out on a third
+ * while state k + 1 is computed; the copies overlap the computation only
+ * when rho_in and rho_out point to page-locked memory.
+ * rho_in, rho_out: n host pointers to [ny][nx] float64 fields (the same
+ * pointer may repeat; rho_out[k] is written when the call returns).
+ * scratch: caller-owned device memory of wblbe_sequence_scratch_bytes()
+ * bytes, 256-byte aligned, not in use by other work.  Synchronises; the
+ * handle then holds the last state (its mass reference that state's
+ * initial mass).  EINVAL: NULL handle or pointer, n < 0, nsteps < 0, short
+ * or misaligned scratch; ECUDA: a failed launch or copy (states before it
+ * are complete). */
+wblbe_status wblbe_run_sequence(wblbe_handle h, int32_t n, const double* const* rho_in,
+                                int64_t nsteps, double* const* rho_out, wblbe_stats* stats,
+                                void* scratch, size_t scratch_bytes);
+
 /* Release the handle (the workspace stays the caller's).  NULL -> EINVAL.
  * Synchronises the stream first. */
 wblbe_status wblbe_destroy(wblbe_handle h);

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -321,8 +322,10 @@ wblbe_status build_graph(wblbe_ctx* h) {
 
 // Moments / stats pass over the current state.  Fields (device pointers, may
 // be null) and the stats record into h->stats_dev.
+// Moments pass over the current state into device fields (any may be null)
+// and its statistics record (stats_out, or the handle's record).
 wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,
-                         double* mu) {
+                         double* mu, double* stats_out = nullptr) {
   const int tile = h->p.nx >= 128 ? 128 : (h->p.nx > 32 ? 64 : 32);
   KParams kp = make_kparams(h, kMomentsRows);
   MomentsOut mo{rho, ux, uy, mu, h->partials};
@@ -330,7 +333,8 @@ wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,
   const int n = h->p.scheme == WBLBE_STANDARD_E6
                     ? e6_partials(h->p.nx, h->p.ny)
                     : ((h->p.nx + tile - 1) / tile) * ((h->p.ny + kMomentsRows - 1) / kMomentsRows);
-  stats_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, n, h->stats_dev);
+  stats_finalize_kernel<<<1, 256, 0, h->stream>>>(h->partials, n,
+                                                  stats_out ? stats_out : h->stats_dev);
   CU(h, cudaGetLastError());
   h->launches += 2;
   return WBLBE_OK;
@@ -511,16 +515,12 @@ wblbe_status wblbe_get_launch(wblbe_handle h, wblbe_launch* launch) {
   return WBLBE_OK;
 }
 
-wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho, int32_t rho_on_device) {
-  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
-  if (!rho) return fail(h, WBLBE_EINVAL, "rho is NULL");
-  DeviceGuard dg(h->device);
-  const double* src = rho;
-  if (!rho_on_device) {
-    CU(h, cudaMemcpyAsync(h->stage, rho, (size_t)h->p.nx * h->p.ny * sizeof(double),
-                          cudaMemcpyHostToDevice, h->stream));
-    src = h->stage;
-  }
+}  // extern "C"
+
+namespace {
+
+// f = f^eq(rho, 0) from a device field, on the handle's stream.
+wblbe_status issue_init(wblbe_ctx* h, const double* src) {
   LayoutParams lp = make_layout_params(h);
   h->cur = 0;
   if (h->p.precision == WBLBE_FP64)
@@ -531,6 +531,25 @@ wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho, int32_t rho_on_de
   h->launches += 1;
   h->steps = 0;
   h->have_state = true;
+  return WBLBE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wblbe_status wblbe_init_rho(wblbe_handle h, const double* rho, int32_t rho_on_device) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (!rho) return fail(h, WBLBE_EINVAL, "rho is NULL");
+  DeviceGuard dg(h->device);
+  const double* src = rho;
+  if (!rho_on_device) {
+    CU(h, cudaMemcpyAsync(h->stage, rho, (size_t)h->p.nx * h->p.ny * sizeof(double),
+                          cudaMemcpyHostToDevice, h->stream));
+    src = h->stage;
+  }
+  wblbe_status st = issue_init(h, src);
+  if (st != WBLBE_OK) return st;
   return reset_mass(h);
 }
 
@@ -720,6 +739,135 @@ wblbe_status wblbe_destroy(wblbe_handle h) {
 }
 
 const char* wblbe_last_error(wblbe_handle h) { return h ? h->err : g_thread_error; }
+
+size_t wblbe_sequence_scratch_bytes(const wblbe_params* params) {
+  if (!params || params->nx < 1 || params->ny < 1) return 0;
+  const size_t field = ((size_t)params->nx * params->ny * sizeof(double) + 255) / 256 * 256;
+  // two input and two output density fields, then two pairs of stats records
+  return 4 * field + 256;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Streams, events and the page-locked statistics buffer of one
+// wblbe_run_sequence call; released (after the streams drain) on every
+// return path.
+struct SequenceRes {
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t ev[8] = {};
+  double* host_rec = nullptr;
+  cudaStream_t compute = nullptr;
+  ~SequenceRes() {
+    if (compute) cudaStreamSynchronize(compute);
+    if (cin) {
+      cudaStreamSynchronize(cin);
+      cudaStreamDestroy(cin);
+    }
+    if (cout) {
+      cudaStreamSynchronize(cout);
+      cudaStreamDestroy(cout);
+    }
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    if (host_rec) cudaFreeHost(host_rec);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+wblbe_status wblbe_run_sequence(wblbe_handle h, int32_t n, const double* const* rho_in,
+                                int64_t nsteps, double* const* rho_out, wblbe_stats* stats,
+                                void* scratch, size_t scratch_bytes) {
+  if (!h) return fail(nullptr, WBLBE_EINVAL, "handle is NULL");
+  if (n < 0 || nsteps < 0) return fail(h, WBLBE_EINVAL, "n and nsteps must be >= 0");
+  if (n == 0) return WBLBE_OK;
+  if (!rho_in || !rho_out || !scratch) return fail(h, WBLBE_EINVAL, "NULL argument");
+  for (int k = 0; k < n; ++k)
+    if (!rho_in[k] || !rho_out[k]) return fail(h, WBLBE_EINVAL, "rho_in[%d] or rho_out[%d] is NULL", k, k);
+  const size_t need = wblbe_sequence_scratch_bytes(&h->p);
+  if (scratch_bytes < need || reinterpret_cast<uintptr_t>(scratch) % 256 != 0)
+    return fail(h, WBLBE_EINVAL, "scratch must hold %zu bytes, 256-byte aligned", need);
+  DeviceGuard dg(h->device);
+  const size_t bytes = (size_t)h->p.nx * h->p.ny * sizeof(double);
+  const size_t field = (bytes + 255) / 256 * 256;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  double* in[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + field)};
+  double* out[2] = {reinterpret_cast<double*>(base + 2 * field),
+                    reinterpret_cast<double*>(base + 3 * field)};
+  // slot b: [initial-state record, final-state record]
+  double* rec = reinterpret_cast<double*>(base + 4 * field);
+  constexpr int kPair = 2 * kStatRec;
+  static_assert(2 * kPair * sizeof(double) <= 256, "stats records fit the scratch tail");
+
+  SequenceRes r;
+  r.compute = h->stream;
+  CU(h, cudaStreamCreateWithFlags(&r.cin, cudaStreamNonBlocking));
+  CU(h, cudaStreamCreateWithFlags(&r.cout, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : r.ev) CU(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t* ev_in = r.ev;        // input b copied
+  cudaEvent_t* ev_used = r.ev + 2;  // input b consumed by the initialisation
+  cudaEvent_t* ev_done = r.ev + 4;  // output b and its records written
+  cudaEvent_t* ev_out = r.ev + 6;   // output b and its records copied out
+  CU(h, cudaHostAlloc(reinterpret_cast<void**>(&r.host_rec), (size_t)n * kPair * sizeof(double),
+                      cudaHostAllocDefault));
+
+  auto h2d = [&](int k) -> wblbe_status {
+    const int b = k & 1;
+    if (k >= 2) CU(h, cudaStreamWaitEvent(r.cin, ev_used[b], 0));
+    CU(h, cudaMemcpyAsync(in[b], rho_in[k], bytes, cudaMemcpyHostToDevice, r.cin));
+    CU(h, cudaEventRecord(ev_in[b], r.cin));
+    return WBLBE_OK;
+  };
+  wblbe_status st = h2d(0);
+  if (st != WBLBE_OK) return st;
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    if (k + 1 < n) {
+      st = h2d(k + 1);           // overlaps state k's steps
+      if (st != WBLBE_OK) return st;
+    }
+    CU(h, cudaStreamWaitEvent(h->stream, ev_in[b], 0));
+    if (k >= 2) CU(h, cudaStreamWaitEvent(h->stream, ev_out[b], 0));
+    st = issue_init(h, in[b]);
+    if (st != WBLBE_OK) return st;
+    CU(h, cudaEventRecord(ev_used[b], h->stream));
+    st = run_moments(h, nullptr, nullptr, nullptr, nullptr, rec + b * kPair);
+    if (st != WBLBE_OK) return st;
+    st = wblbe_step(h, nsteps);
+    if (st != WBLBE_OK) return st;
+    st = run_moments(h, out[b], nullptr, nullptr, nullptr, rec + b * kPair + kStatRec);
+    if (st != WBLBE_OK) return st;
+    CU(h, cudaEventRecord(ev_done[b], h->stream));
+    // state k's results leave while state k + 1 is computed
+    CU(h, cudaStreamWaitEvent(r.cout, ev_done[b], 0));
+    CU(h, cudaMemcpyAsync(rho_out[k], out[b], bytes, cudaMemcpyDeviceToHost, r.cout));
+    CU(h, cudaMemcpyAsync(r.host_rec + (size_t)k * kPair, rec + b * kPair, kPair * sizeof(double),
+                          cudaMemcpyDeviceToHost, r.cout));
+    CU(h, cudaEventRecord(ev_out[b], r.cout));
+  }
+  CU(h, cudaStreamSynchronize(r.cout));
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (int k = 0; k < n; ++k) {
+    const double* v0 = r.host_rec + (size_t)k * kPair;
+    const double* v = v0 + kStatRec;
+    if (k == n - 1) h->mass0 = v0[0];   // the handle keeps the last state
+    if (!stats) continue;
+    wblbe_stats& o = stats[k];
+    o.step = nsteps;
+    o.mass = v[0];
+    o.kinetic = v[1];
+    o.umax = v[2];
+    o.mu_min = v[3];
+    o.mu_max = v[4];
+    o.nonfinite = v[5] != 0.0 || !std::isfinite(v[0]);
+    o.mass_drift_rel = v0[0] != 0.0 ? (v[0] - v0[0]) / v0[0] : 0.0;
+  }
+  return WBLBE_OK;
+}
 
 }  // extern "C"
 

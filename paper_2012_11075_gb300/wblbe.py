@@ -93,6 +93,9 @@ _SIGNATURES = {
     "wblbe_set_populations": (ctypes.c_int, [_H, _P, ctypes.c_int32]),
     "wblbe_step_count": (ctypes.c_int64, [_H]),
     "wblbe_set_step_count": (ctypes.c_int, [_H, ctypes.c_int64]),
+    "wblbe_sequence_scratch_bytes": (ctypes.c_size_t, [_P]),
+    "wblbe_run_sequence": (ctypes.c_int, [_H, ctypes.c_int32, _P, ctypes.c_int64, _P, _P, _P,
+                                          ctypes.c_size_t]),
     "wblbe_kernel_launches": (ctypes.c_int64, [_H]),
     "wblbe_destroy": (ctypes.c_int, [_H]),
     "wblbe_last_error": (ctypes.c_char_p, [_H]),
@@ -363,6 +366,42 @@ class Solver:
     @property
     def steps(self) -> int:
         return int(self.lib.wblbe_step_count(self.h))
+
+    def run_sequence(self, rho_in, nsteps: int, rho_out) -> list:
+        """Relax len(rho_in) initial states one after another, each for nsteps
+        steps from f = f^eq(rho, 0), with the host copies overlapping the
+        computation (page-locked CPU tensors or numpy arrays; pinned memory
+        is what lets the copies overlap).  rho_in, rho_out: equal-length
+        lists of host float64 (ny, nx) arrays/tensors (entries may repeat;
+        rho_out entries must be writable).  Returns the stats of each final
+        state.  The device scratch is allocated once per solver."""
+        _require(len(rho_in) == len(rho_out), "rho_in and rho_out must have the same length")
+        n = len(rho_in)
+
+        def host_ptr(a, writable):
+            if isinstance(a, np.ndarray):
+                ok = (a.dtype == np.float64 and a.flags.c_contiguous
+                      and (a.flags.writeable or not writable))
+                ptr = a.ctypes.data
+            else:
+                ok = (a.dtype == self._torch.float64 and a.is_contiguous()
+                      and not a.is_cuda)
+                ptr = a.data_ptr()
+            _require(ok and tuple(a.shape) == self.shape,
+                     f"states must be contiguous host float64 arrays of shape {self.shape}")
+            return ptr
+
+        pin = (ctypes.c_void_p * max(n, 1))(*[host_ptr(a, False) for a in rho_in])
+        pout = (ctypes.c_void_p * max(n, 1))(*[host_ptr(a, True) for a in rho_out])
+        need = int(self.lib.wblbe_sequence_scratch_bytes(ctypes.byref(self._cp)))
+        if getattr(self, "_seq_scratch", None) is None or self._seq_scratch.numel() < need:
+            self._seq_scratch = self._torch.empty(need, dtype=self._torch.uint8, device="cuda")
+        stats = (CStats * max(n, 1))()
+        self._check(self.lib.wblbe_run_sequence(
+            self.h, n, ctypes.cast(pin, ctypes.c_void_p), int(nsteps),
+            ctypes.cast(pout, ctypes.c_void_p), ctypes.cast(stats, ctypes.c_void_p),
+            ctypes.c_void_p(self._seq_scratch.data_ptr()), self._seq_scratch.numel()))
+        return [stats[k].as_dict() for k in range(n)]
 
     def set_step_count(self, step: int):
         """Restore the step counter (e.g. when resuming a checkpoint); in FP32
