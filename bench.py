@@ -334,7 +334,16 @@ def run_batched(args, stream, torch):
     from paper_2012_11075_gb300 import autotune, wblbe
     from paper_2012_11075_gb300 import workloads as wl
     specs = wl.batched_case_specs(count=args.batch_cases, seed=4)
+    if args.batch_uniform:
+        # equal cases instead of the mix (to separate the costs of ragged
+        # strips from those of the queue): droplets of radius side/5, W = 4,
+        # ratio 10, tau = 1.0 (stable, so every case runs its full budget)
+        ux, uy, count = (int(v) for v in args.batch_uniform.split(","))
+        beta = wl.beta_for_width(0.01, 4.0, 1.0, 0.1)
+        specs = [dict(k=k, nx=ux, ny=uy, kind="droplet", frac=0.2, rho_l=1.0, rho_g=0.1,
+                      tau=1.0, kappa=0.01, width=4.0, beta=beta) for k in range(count)]
     gpu = torch.cuda.get_device_name()
+    max_nodes = max(512 * 512, max(sp["nx"] * sp["ny"] for sp in specs))
 
     def params(sp, tau=None):
         return wblbe.Params(sp["nx"], sp["ny"], sp["tau"] if tau is None else tau, sp["kappa"],
@@ -353,7 +362,7 @@ def run_batched(args, stream, torch):
         # cases all keep running while the candidates are timed (the same
         # lattices with tau >= 0.9, above the WB stability limit: the work
         # per launch does not depend on tau)
-        tb = wblbe.Batch(max_cases=len(specs), max_tiles=1 << 18, max_case_nodes=512 * 512,
+        tb = wblbe.Batch(max_cases=len(specs), max_tiles=1 << 18, max_case_nodes=max_nodes,
                          arena_bytes=int(sum(case_bytes) * 1.02) + (1 << 20), stream=stream)
         for sp in specs:
             tb.admit(params(sp, max(sp["tau"], 0.9)), wl.case_field(sp), 0.0, 10 ** 9)
@@ -361,7 +370,7 @@ def run_batched(args, stream, torch):
                               sync=torch.cuda.synchronize)
         tb.close()
     cfg = tuned["config"]
-    b = wblbe.Batch(max_cases=len(specs), max_tiles=1 << 18, max_case_nodes=512 * 512,
+    b = wblbe.Batch(max_cases=len(specs), max_tiles=1 << 18, max_case_nodes=max_nodes,
                     arena_bytes=int(sum(case_bytes) * 1.02) + (1 << 20), tile_x=cfg[0],
                     rows_per_tile=cfg[1], steps_per_launch=cfg[2], stream=stream)
     fields = [wl.case_field(sp) for sp in specs]
@@ -392,7 +401,9 @@ def run_batched(args, stream, torch):
         by_state.setdefault(str(infos[cid]["state"]), []).append(l)
     launches = b.kernel_launches - l0
     b.close()
-    return {"workload": f"batched_{len(specs)}_uneven_cases_wb_fp32",
+    name = (f"batched_{len(specs)}_equal_{specs[0]['nx']}x{specs[0]['ny']}_cases_wb_fp32"
+            if args.batch_uniform else f"batched_{len(specs)}_uneven_cases_wb_fp32")
+    return {"workload": name,
             "cases": len(specs), "nodes": int(sum(nodes.values())),
             "steps_per_case": args.batch_steps, "config": cfg,
             "tuned_from_cache": tuned.get("cached", False), "tuning_mlups": tuned.get("candidates"),
@@ -739,6 +750,9 @@ def main():
     ap.add_argument("--no-ratio50", action="store_true")
     ap.add_argument("--batch-cases", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--batch-uniform", default=None,
+                    help="NX,NY,COUNT: the batched leg on COUNT equal droplet cases instead "
+                         "of the uneven mix")
     ap.add_argument("--batch-config", default=None,
                     help="tile_x,rows_per_tile,steps_per_launch for the batched leg "
                          "(default: chosen by the autotuner)")
