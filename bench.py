@@ -324,6 +324,38 @@ def time_e2e(solver, rho_pinned, rho_outs_pinned, substeps, steps, warmup, torch
     return dt
 
 
+def run_slabs(args, stream, torch, single_kernel_mlups):
+    """The headline lattice (4096^2, 64 droplets, ratio 10, FP32 WB) split into
+    N row slabs on this one GPU (each slab with 3 ghost rows per side, one
+    exchange per step; the slabs' kernels run side by side on forked streams
+    and chunks of steps replay from a CUDA graph): MLUPS against the
+    single-lattice step kernel, i.e. what the decomposition itself costs."""
+    from paper_2012_11075_gb300 import wblbe
+    pr = make_problem(args.lattice)
+    params = wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l, pr.rho_g,
+                          scheme=wblbe.WELL_BALANCED, precision=wblbe.FP32_SHIFTED)
+    out = []
+    for n in (1, 2, 4, 8):
+        s = wblbe.Slabs(params, n, stream=stream)
+        s.init_rho(pr.rho)
+        s.step(32)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        steps = 192
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            s.step(steps)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1e3
+        st = s.stats()
+        s.close()
+        mlups = pr.nx * pr.ny * steps / dt / 1e6
+        out.append({"nslabs": n, "mlups": mlups, "vs_single_kernel": mlups / single_kernel_mlups,
+                    "nonfinite": bool(st["nonfinite"])})
+    return {"workload": WORKLOAD + ", row slabs on one GPU", "steps": 192, "results": out}
+
+
 def run_batched(args, stream, torch):
     """The uneven batched case mix: 512 independent cases (sides 64..512
     log-uniform, flat/droplet, ratio 2..50, tau 0.55..1.2), FP32-shifted
@@ -602,6 +634,26 @@ def run_ours(args, world, rank, local):
         if rank == 0:
             print(json.dumps({"d3q19": run_d3q19(args, stream, torch)}), flush=True)
         return 0
+    if args.only == "slabs":
+        # against the single-lattice step kernel's rate measured here
+        if rank == 0:
+            sol = wblbe.Solver(wblbe.Params(pr.nx, pr.ny, pr.tau, pr.kappa, pr.beta, pr.rho_l,
+                                            pr.rho_g, scheme=wblbe.WELL_BALANCED,
+                                            precision=wblbe.FP32_SHIFTED), stream=stream)
+            sol.init_rho(pr.rho)
+            sol.step(32)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                sol.step(192)
+                ev[1].record(stream)
+            torch.cuda.synchronize()
+            single = pr.nx * pr.ny * 192 / (ev[0].elapsed_time(ev[1]) / 1e3) / 1e6
+            sol.close()
+            print(json.dumps({"slabs": run_slabs(args, stream, torch, single),
+                              "single_lattice_mlups": single}), flush=True)
+        return 0
     results = {}
     precisions = [("f32", wblbe.FP32_SHIFTED, pr), ("f64", wblbe.FP64, pr)]
     if args.only != "both":
@@ -717,6 +769,8 @@ def run_ours(args, world, rank, local):
         line["schemes"] = run_schemes(args, stream, torch)
     if not args.no_d3q19:
         line["d3q19"] = run_d3q19(args, stream, torch, fp64_peak)
+    if not args.no_slabs:
+        line["slabs"] = run_slabs(args, stream, torch, r32["kern_mlups"])
     if not args.no_batched:
         line["batched"] = run_batched(args, stream, torch)
         if not args.no_serving:
@@ -739,12 +793,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lattice", type=int, default=4096,
                     help="lattice side (4096 is the benchmark; smaller sides are for profiling)")
-    ap.add_argument("--only", choices=["both", "f32", "f64", "batched", "schemes", "d3q19"],
+    ap.add_argument("--only", choices=["both", "f32", "f64", "batched", "schemes", "d3q19",
+                                       "slabs"],
                     default="both")
     ap.add_argument("--no-d3q19", action="store_true")
     ap.add_argument("--d3-lattice", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-slabs", action="store_true")
     ap.add_argument("--no-schemes", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-ratio50", action="store_true")

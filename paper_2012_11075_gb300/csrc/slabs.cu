@@ -20,11 +20,15 @@
 // order as in the whole lattice, and the FP32 rounding draws use the global
 // row, so results equal the single-lattice run bit for bit.
 //
-// On one device the exchange is two device-to-device copies per slab and
-// step on the caller's stream.  The row partition and the exchange plan are
-// what a run across devices would also use.
+// On one device the slabs' kernels of a step run side by side on forked
+// streams (each covers 1/nslabs of the rows, so together they fill the GPU
+// as one whole-lattice launch does), then one kernel copies every slab's
+// ghost rows; chunks of kSlabGraphSteps steps replay from a captured CUDA
+// graph.  The row partition and the exchange plan are what a run across
+// devices would also use.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -40,6 +44,7 @@ using namespace wblbe;
 namespace {
 
 constexpr int kGhost = 3;                 // ghost rows on each side of a slab
+constexpr int kSlabGraphSteps = 16;       // steps per graph replay (even)
 constexpr size_t kAlignS = 256;
 constexpr int kSlabMomentsRows = 16;
 
@@ -158,10 +163,18 @@ struct wblbe_slabs {
   std::vector<Slab> slabs;
   int cur;
   int tile_x, rows_per_cta;
+  std::vector<int> slab_rows;    // rows per CTA of each slab's step launch
   double* stage;                 // nx * ny float64 (host I/O)
   double* partials;
   int max_records;
   double* stats_dev;
+  long long* step_dev;           // step of the first step of a graph replay
+  void* xdesc;                   // exchange table (XSlab[nslabs]) in the workspace
+  std::vector<cudaStream_t> side;  // nslabs - 1 streams for the slabs' kernels
+  std::vector<cudaEvent_t> ev;     // fork event, then one join event per side stream
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
   int64_t steps, launches;
   double mass0;
   bool have_state;
@@ -190,11 +203,19 @@ struct SlabLayout {
   int pitch;
   size_t elem;
   std::vector<size_t> off_buf;   // 2 per slab
-  size_t off_stage, off_partials, off_stats, total;
+  size_t off_stage, off_partials, off_stats, off_step, off_xdesc, total;
   int max_records;
 };
 
 int slab_tile(int nx) { return nx >= 128 ? 128 : (nx > 32 ? 64 : 32); }
+
+// A slab as the exchange kernel sees it.
+struct XSlab {
+  unsigned char* buf[2];
+  long long plane_bytes;         // bytes per population plane
+  int n;                         // owned rows
+  int pad;
+};
 
 SlabLayout slab_layout(const wblbe_params* p, int nslabs) {
   SlabLayout L{};
@@ -217,6 +238,8 @@ SlabLayout slab_layout(const wblbe_params* p, int nslabs) {
   L.off_stage = off; off += align_s((size_t)p->nx * p->ny * sizeof(double));
   L.off_partials = off; off += align_s((size_t)records * kStatRec * sizeof(double));
   L.off_stats = off; off += align_s(8 * sizeof(double));
+  L.off_step = off; off += align_s(sizeof(long long));
+  L.off_xdesc = off; off += align_s(sizeof(XSlab) * nslabs);
   L.total = off;
   return L;
 }
@@ -246,30 +269,95 @@ KParams slab_kparams(const wblbe_slabs* h, int k, int rows) {
 }
 
 cudaError_t slab_launch(const wblbe_slabs* h, int mode, const void* src, void* dst,
-                        const KParams& kp, const MomentsOut& mo, int tile) {
+                        const KParams& kp, const MomentsOut& mo, int tile,
+                        cudaStream_t stream = nullptr) {
   return launch_strip_any(h->p.scheme, h->p.precision == WBLBE_FP64, mode, src, dst, kp, mo,
-                          tile, h->stream);
+                          tile, stream ? stream : h->stream);
 }
 
-// Ghost rows of every slab's buffer `which` from its neighbours' owned rows.
-wblbe_status exchange(wblbe_slabs* h, int which) {
+// Ghost rows of every slab's buffer `which` from its neighbours' owned rows,
+// in 16-byte pieces (rows are whole multiples of 128 bytes): blockIdx.z is
+// the slab; blockIdx.y the side (lower ghosts <- the last 3 owned rows of
+// the slab below; upper ghosts <- the first 3 owned rows of the slab above),
+// the ghost row and the plane.
+__global__ void __launch_bounds__(128)
+    slab_exchange_kernel(const XSlab* __restrict__ xs, int nslabs, int which, int row_pieces) {
+  const int k = blockIdx.z;
+  const int q = blockIdx.y;                 // 0 .. 2 * kGhost * 9 - 1
+  const int side = q / (kGhost * 9), r = (q / 9) % kGhost, i = q % 9;
+  const XSlab me = xs[k];
+  const XSlab nb = xs[side == 0 ? (k + nslabs - 1) % nslabs : (k + 1) % nslabs];
+  const long long row_bytes = (long long)row_pieces * 16;
+  const int dst_row = side == 0 ? r : kGhost + me.n + r;
+  const int src_row = side == 0 ? nb.n + r : kGhost + r;
+  const uint4* src = reinterpret_cast<const uint4*>(nb.buf[which] + i * nb.plane_bytes +
+                                                    src_row * row_bytes);
+  uint4* dst = reinterpret_cast<uint4*>(me.buf[which] + i * me.plane_bytes + dst_row * row_bytes);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < row_pieces; c += gridDim.x * blockDim.x)
+    dst[c] = src[c];
+}
+
+__global__ void slab_set_step_kernel(long long* dst, long long v) { *dst = v; }
+
+wblbe_status exchange(wblbe_slabs* h, int which, cudaStream_t stream) {
+  const int row_pieces = (int)((size_t)h->pitch * h->elem / 16);
+  dim3 grid((row_pieces + 127) / 128, 2 * kGhost * 9, h->nslabs);
+  slab_exchange_kernel<<<grid, 128, 0, stream>>>(static_cast<const XSlab*>(h->xdesc), h->nslabs,
+                                                 which, row_pieces);
+  SCU(h, cudaGetLastError());
+  return WBLBE_OK;
+}
+
+// One step from buffer `from` on `stream`: the slabs' kernels side by side
+// (slab 0 on `stream`, slab k on side stream k - 1, forked from and joined
+// back into `stream` by events), then the exchange.  The FP32 draws take
+// the step t = step + *step_base (step_base may be null).
+wblbe_status issue_slab_step(wblbe_slabs* h, int from, cudaStream_t stream, long long step,
+                             const long long* step_base) {
   const int S = h->nslabs;
-  const size_t row_bytes = (size_t)h->pitch * h->elem;
-  for (int k = 0; k < S; ++k) {
-    auto& me = h->slabs[k];
-    const auto& below = h->slabs[(k + S - 1) % S];
-    const auto& above = h->slabs[(k + 1) % S];
-    // lower ghosts [0, 3) <- the last 3 owned rows of the slab below
-    SCU(h, cudaMemcpy2DAsync(me.buf[which], me.plane * h->elem,
-                             below.buf[which] + (size_t)below.n * row_bytes,
-                             below.plane * h->elem, kGhost * row_bytes, 9,
-                             cudaMemcpyDeviceToDevice, h->stream));
-    // upper ghosts [3 + n, 6 + n) <- the first 3 owned rows of the slab above
-    SCU(h, cudaMemcpy2DAsync(me.buf[which] + (size_t)(kGhost + me.n) * row_bytes,
-                             me.plane * h->elem, above.buf[which] + (size_t)kGhost * row_bytes,
-                             above.plane * h->elem, kGhost * row_bytes, 9,
-                             cudaMemcpyDeviceToDevice, h->stream));
+  if (S > 1) {
+    SCU(h, cudaEventRecord(h->ev[0], stream));
+    for (int k = 1; k < S; ++k) SCU(h, cudaStreamWaitEvent(h->side[k - 1], h->ev[0], 0));
   }
+  for (int k = 0; k < S; ++k) {
+    KParams kp = slab_kparams(h, k, h->slab_rows[k]);
+    kp.step = step;
+    kp.step_base = step_base;
+    MomentsOut mo{};
+    SCU(h, slab_launch(h, kModeStep, h->slabs[k].buf[from], h->slabs[k].buf[1 - from], kp, mo,
+                       h->tile_x, k == 0 ? stream : h->side[k - 1]));
+  }
+  for (int k = 1; k < S; ++k) {
+    SCU(h, cudaEventRecord(h->ev[k], h->side[k - 1]));
+    SCU(h, cudaStreamWaitEvent(stream, h->ev[k], 0));
+  }
+  return exchange(h, 1 - from, stream);
+}
+
+void drop_slab_graph(wblbe_slabs* h) {
+  if (h->graph_valid) cudaGraphExecDestroy(h->graph);
+  h->graph_valid = false;
+}
+
+// kSlabGraphSteps steps from buffer 0, the steps' indices relative to the
+// base word step_dev (set before every replay).
+wblbe_status build_slab_graph(wblbe_slabs* h) {
+  drop_slab_graph(h);
+  cudaGraph_t g = nullptr;
+  SCU(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  wblbe_status st = WBLBE_OK;
+  for (int k = 0; k < kSlabGraphSteps && st == WBLBE_OK; ++k)
+    st = issue_slab_step(h, k & 1, h->capture_stream, k, h->step_dev);
+  cudaError_t ce = cudaStreamEndCapture(h->capture_stream, &g);
+  if (st != WBLBE_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    if (st != WBLBE_OK) return st;
+    return sfail(h, WBLBE_ECUDA, "slab graph capture: %s", cudaGetErrorString(ce));
+  }
+  cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return sfail(h, WBLBE_ECUDA, "slab graph instantiate: %s", cudaGetErrorString(ie));
+  h->graph_valid = true;
   return WBLBE_OK;
 }
 
@@ -385,9 +473,40 @@ wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs, void
   h->partials = reinterpret_cast<double*>(ws + L.off_partials);
   h->max_records = L.max_records;
   h->stats_dev = reinterpret_cast<double*>(ws + L.off_stats);
+  h->step_dev = reinterpret_cast<long long*>(ws + L.off_step);
+  h->xdesc = ws + L.off_xdesc;
   h->cur = 0;
-  // launch shape: 128-column strips and, for every slab, one run of rows per
-  // resident CTA as the single-lattice default does (even rows, at least 8)
+  {
+    // the exchange table, streams and events of the step
+    std::vector<XSlab> xs;
+    for (const auto& s : h->slabs)
+      xs.push_back(XSlab{{s.buf[0], s.buf[1]}, s.plane * (long long)L.elem, s.n, 0});
+    cudaError_t e = cudaMemcpy(h->xdesc, xs.data(), xs.size() * sizeof(XSlab),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking);
+    for (int k = 1; k < nslabs && e == cudaSuccess; ++k) {
+      cudaStream_t st = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) h->side.push_back(st);
+    }
+    for (int k = 0; k < nslabs && e == cudaSuccess; ++k) {
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) h->ev.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+      for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+      for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
+      if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+      delete h;
+      return sfail(nullptr, WBLBE_ECUDA, "slab streams: %s", cudaGetErrorString(e));
+    }
+  }
+  // launch shape: 128-column strips, and runs of rows such that the slabs'
+  // step launches together make one resident wave, as the single-lattice
+  // default does for the whole lattice: B = resident CTAs / strips row runs
+  // shared out over the slabs in proportion to their rows (each at least
+  // one; even rows, at least 8)
   h->tile_x = slab_tile(params->nx);
   {
     int nsm = 152, dev = 0;
@@ -396,13 +515,30 @@ wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs, void
     const int per_sm =
         resident_strip_any(params->scheme, params->precision == WBLBE_FP64, h->tile_x);
     const long long strips = (params->nx + h->tile_x - 1) / h->tile_x;
-    long long segs = (long long)per_sm * nsm / strips / nslabs;
-    if (segs < 1) segs = 1;
-    const int nmax = params->ny / nslabs + 2;
-    long long rows = (nmax + segs - 1) / segs;
-    if (rows < 8) rows = 8;
-    rows += rows & 1;
-    h->rows_per_cta = (int)rows;
+    const long long B = std::max<long long>((long long)per_sm * nsm / strips, nslabs);
+    std::vector<long long> segs(nslabs);
+    long long total = 0;
+    for (int k = 0; k < nslabs; ++k) {
+      segs[k] = std::max<long long>(1, (B * h->slabs[k].n + params->ny / 2) / params->ny);
+      total += segs[k];
+    }
+    // take runs back from the slabs with the most until the total fits
+    while (total > B) {
+      int kmax = 0;
+      for (int k = 1; k < nslabs; ++k)
+        if (segs[k] > segs[kmax]) kmax = k;
+      if (segs[kmax] <= 1) break;
+      --segs[kmax];
+      --total;
+    }
+    h->rows_per_cta = 8;
+    for (int k = 0; k < nslabs; ++k) {
+      long long rows = (h->slabs[k].n + segs[k] - 1) / segs[k];
+      if (rows < 8) rows = 8;
+      rows += rows & 1;
+      h->slab_rows.push_back((int)rows);
+      h->rows_per_cta = std::max(h->rows_per_cta, (int)rows);
+    }
   }
   *out = h;
   return WBLBE_OK;
@@ -451,18 +587,39 @@ wblbe_status wblbe_slabs_step(wblbe_slabs_handle h, int64_t nsteps) {
   if (nsteps < 0) return sfail(h, WBLBE_EINVAL, "nsteps must be >= 0");
   if (!h->have_state) return sfail(h, WBLBE_EINVAL, "no state: call wblbe_slabs_init_rho first");
   DevGuard dg(h->device);
-  for (int64_t n = 0; n < nsteps; ++n) {
-    for (int k = 0; k < h->nslabs; ++k) {
-      KParams kp = slab_kparams(h, k, h->rows_per_cta);
-      MomentsOut mo{};
-      SCU(h, slab_launch(h, kModeStep, h->slabs[k].buf[h->cur], h->slabs[k].buf[1 - h->cur], kp,
-                         mo, h->tile_x));
-      h->launches += 1;
-    }
-    wblbe_status st = exchange(h, 1 - h->cur);
+  const int per_step = h->nslabs + 1;       // the slabs' kernels and the exchange
+  auto direct = [&]() -> wblbe_status {
+    wblbe_status st = issue_slab_step(h, h->cur, h->stream, h->steps, nullptr);
     if (st != WBLBE_OK) return st;
     h->cur ^= 1;
     h->steps += 1;
+    h->launches += per_step;
+    return WBLBE_OK;
+  };
+  int64_t left = nsteps;
+  if (left >= kSlabGraphSteps) {
+    if (!h->graph_valid) {
+      wblbe_status st = build_slab_graph(h);
+      if (st != WBLBE_OK) return st;
+    }
+    // the graph starts from buffer 0
+    if (h->cur == 1) {
+      wblbe_status st = direct();
+      if (st != WBLBE_OK) return st;
+      --left;
+    }
+    while (left >= kSlabGraphSteps) {
+      slab_set_step_kernel<<<1, 1, 0, h->stream>>>(h->step_dev, h->steps);
+      SCU(h, cudaGetLastError());
+      SCU(h, cudaGraphLaunch(h->graph, h->stream));
+      h->launches += (int64_t)kSlabGraphSteps * per_step + 1;
+      h->steps += kSlabGraphSteps;
+      left -= kSlabGraphSteps;
+    }
+  }
+  for (; left > 0; --left) {
+    wblbe_status st = direct();
+    if (st != WBLBE_OK) return st;
   }
   return WBLBE_OK;
 }
@@ -536,6 +693,10 @@ wblbe_status wblbe_slabs_destroy(wblbe_slabs_handle h) {
   {
     DevGuard dg(h->device);
     cudaStreamSynchronize(h->stream);
+    drop_slab_graph(h);
+    for (cudaStream_t st : h->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : h->ev) cudaEventDestroy(ev);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   }
   delete h;
   return WBLBE_OK;

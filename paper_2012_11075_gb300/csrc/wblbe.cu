@@ -320,8 +320,6 @@ wblbe_status build_graph(wblbe_ctx* h) {
   return WBLBE_OK;
 }
 
-// Moments / stats pass over the current state.  Fields (device pointers, may
-// be null) and the stats record into h->stats_dev.
 // Moments pass over the current state into device fields (any may be null)
 // and its statistics record (stats_out, or the handle's record).
 wblbe_status run_moments(wblbe_ctx* h, double* rho, double* ux, double* uy,

@@ -1,6 +1,8 @@
 """One lattice split into row slabs (wblbe_slabs_*), through the C ABI on
 one GPU: every slab is advanced from its own rows and 3 ghost rows on each
-side, exchanged by device copies after every step; the result must equal
+side, exchanged by one copy kernel after every step (the slabs' kernels run
+side by side on forked streams; chunks of steps replay from a CUDA graph);
+the result must equal
 the single-lattice run bit for bit (populations, fields and the
 order-independent statistics), in both precisions and for every number of
 slabs, including one slab whose ghost rows wrap onto itself."""
@@ -66,3 +68,28 @@ def test_slabs_refuse_thin_slabs_and_the_e6_variant():
         wblbe.Slabs(gpu_params(pr, wblbe.WELL_BALANCED), 12)     # slabs of 2 rows
     with pytest.raises(wblbe.WblbeError):
         wblbe.Slabs(gpu_params(pr, wblbe.STANDARD_E6), 2)
+
+
+@pytest.mark.parametrize("precision", [wblbe.FP64, wblbe.FP32_SHIFTED])
+def test_slabs_graph_chunks_and_direct_steps(precision):
+    """Steps issued in uneven chunks (1, 20, 17, 33: graph replays starting
+    from either buffer, and direct steps) equal the single lattice stepped
+    the same way, bit for bit, and count their steps and launches."""
+    pr = wl.droplet(n=96, radius=20.0, tau=0.9, nx=96, ny=90)
+    a = wblbe.Solver(gpu_params(pr, wblbe.WELL_BALANCED, precision))
+    b = wblbe.Slabs(gpu_params(pr, wblbe.WELL_BALANCED, precision), 5)
+    a.init_rho(pr.rho)
+    b.init_rho(pr.rho)
+    l0 = b.kernel_launches
+    for n in (1, 20, 17, 33):
+        a.step(n)
+        b.step(n)
+    assert a.steps == b.steps == 71
+    # 71 steps of 5 slab kernels and one exchange each, plus one step-base
+    # kernel per graph replay of 16 steps: 1 -> 1 direct; 20 -> 1 direct
+    # (the state is in the second buffer), 1 replay, 3 direct; 17 -> 1
+    # direct, 1 replay; 33 -> 2 replays, 1 direct
+    assert b.kernel_launches - l0 == 71 * 6 + 4
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    a.close()
+    b.close()
