@@ -47,10 +47,10 @@ SUBSTEPS = {"f32": 200, "f64": 40}              # lattice steps per benchmark st
 # instruction mix (2 x DFMA + DADD + DMUL per node, halo work included;
 # 2048^2 well-balanced case: DADD 41.5, DMUL 21.2, DFMA 48.75)
 FP64_FLOPS_PER_LU = 160.3
-# FP64 flops per lattice update of the three D3Q19 kernels (density 19 DADD;
-# chemical potential 39 DADD + 4 DMUL + 2 DFMA; collide 78 DADD + 32 DMUL +
+# FP64 flops per lattice update of the three D3Q19 kernels (density 18 DADD;
+# chemical potential 19 DADD + 4 DMUL + 4 DFMA; collide 78 DADD + 32 DMUL +
 # 81 DFMA; ncu op mix on a 128^3 droplet, one thread per node, no halo work)
-D3_FLOPS_PER_LU = 338.0
+D3_FLOPS_PER_LU = 321.0
 # oldest state (lattice steps since initialisation) a timed step may start
 # from; see time_device
 MAX_STATE_AGE = 1200
