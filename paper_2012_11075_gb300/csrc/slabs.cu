@@ -503,10 +503,14 @@ wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs, void
     }
   }
   // launch shape: 128-column strips, and runs of rows such that the slabs'
-  // step launches together make one resident wave, as the single-lattice
-  // default does for the whole lattice: B = resident CTAs / strips row runs
-  // shared out over the slabs in proportion to their rows (each at least
-  // one; even rows, at least 8)
+  // step launches together make whole resident waves, as the single-lattice
+  // default does for the whole lattice: m * B row runs (B = resident CTAs /
+  // strips) shared out over the slabs in proportion to their rows, each
+  // slab at least one (even rows, at least 8).  m = 1 unless the runs of
+  // different slabs would then differ by more than a quarter in length
+  // (8 slabs of 512 rows in 23 runs: 172 and 256), which leaves the longest
+  // runs running alone at the end of every step; then the fewest waves
+  // (up to 4) that bring them within it.
   h->tile_x = slab_tile(params->nx);
   {
     int nsm = 152, dev = 0;
@@ -515,30 +519,40 @@ wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs, void
     const int per_sm =
         resident_strip_any(params->scheme, params->precision == WBLBE_FP64, h->tile_x);
     const long long strips = (params->nx + h->tile_x - 1) / h->tile_x;
-    const long long B = std::max<long long>((long long)per_sm * nsm / strips, nslabs);
-    std::vector<long long> segs(nslabs);
-    long long total = 0;
-    for (int k = 0; k < nslabs; ++k) {
-      segs[k] = std::max<long long>(1, (B * h->slabs[k].n + params->ny / 2) / params->ny);
-      total += segs[k];
+    const long long B = std::max<long long>((long long)per_sm * nsm / strips, 1);
+    std::vector<int> best;
+    for (int m = 1; m <= 4; ++m) {
+      const long long Bm = std::max<long long>(m * B, nslabs);
+      std::vector<long long> segs(nslabs);
+      long long total = 0;
+      for (int k = 0; k < nslabs; ++k) {
+        segs[k] = std::max<long long>(1, (Bm * h->slabs[k].n + params->ny / 2) / params->ny);
+        total += segs[k];
+      }
+      // take runs back from the slabs with the most until the total fits
+      while (total > Bm) {
+        int kmax = 0;
+        for (int k = 1; k < nslabs; ++k)
+          if (segs[k] > segs[kmax]) kmax = k;
+        if (segs[kmax] <= 1) break;
+        --segs[kmax];
+        --total;
+      }
+      std::vector<int> rows_k;
+      int lo = 1 << 30, hi = 0;
+      for (int k = 0; k < nslabs; ++k) {
+        long long rows = (h->slabs[k].n + segs[k] - 1) / segs[k];
+        if (rows < 8) rows = 8;
+        rows += rows & 1;
+        rows_k.push_back((int)rows);
+        lo = std::min(lo, (int)rows);
+        hi = std::max(hi, (int)rows);
+      }
+      best = rows_k;
+      if (4 * hi <= 5 * lo) break;
     }
-    // take runs back from the slabs with the most until the total fits
-    while (total > B) {
-      int kmax = 0;
-      for (int k = 1; k < nslabs; ++k)
-        if (segs[k] > segs[kmax]) kmax = k;
-      if (segs[kmax] <= 1) break;
-      --segs[kmax];
-      --total;
-    }
-    h->rows_per_cta = 8;
-    for (int k = 0; k < nslabs; ++k) {
-      long long rows = (h->slabs[k].n + segs[k] - 1) / segs[k];
-      if (rows < 8) rows = 8;
-      rows += rows & 1;
-      h->slab_rows.push_back((int)rows);
-      h->rows_per_cta = std::max(h->rows_per_cta, (int)rows);
-    }
+    h->slab_rows = best;
+    h->rows_per_cta = *std::max_element(best.begin(), best.end());
   }
   *out = h;
   return WBLBE_OK;
