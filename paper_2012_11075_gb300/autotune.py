@@ -15,11 +15,11 @@ import os
 import time
 from pathlib import Path
 
-# strip width x rows per tile x steps per launch; 1-16 steps per launch were
-# never chosen on the benchmark mix (the per-launch host check and the
-# launch tail weigh too much)
-DEFAULT_CANDIDATES = [(tx, rows, k) for tx in (64, 128, 256) for rows in (16, 32, 64, 128)
-                      for k in (32, 64)]
+# strip width x rows per tile x steps per launch; 1-16 steps per launch and
+# 16-row tiles were never chosen on the benchmark mix (the per-launch host
+# check, the launch tail and the halo rows weigh too much)
+DEFAULT_CANDIDATES = [(tx, rows, k) for tx in (64, 128, 256) for rows in (32, 64, 128)
+                      for k in (32, 64, 128)]
 
 
 def cache_path() -> Path:
