@@ -352,10 +352,14 @@ const char* wblbe_batch_last_error(wblbe_batch_handle b);
  * own rows and 3 ghost rows on each side, with one exchange of ghost rows
  * per step.  These entry points do that on one device: nslabs slabs of
  * near-equal row counts (boundaries on even rows, every slab >= 3 rows),
- * stepped by the single-lattice kernels and exchanged by device-to-device
- * copies, with results equal bit for bit to a wblbe_create handle of the
- * same parameters (schemes 0-3; the E6 variant is refused).  Conventions,
- * arrays, workspace and stream rules are those of the single-lattice API. */
+ * stepped by the single-lattice kernels, the slabs' launches side by side
+ * on streams the handle creates (forked from and joined back into the
+ * caller's stream by events), and exchanged by one copy kernel per step,
+ * with results equal bit for bit to a wblbe_create handle of the same
+ * parameters (schemes 0-3; the E6 variant is refused).  Chunks of 16 steps
+ * replay from a captured CUDA graph.  Conventions, arrays, workspace and
+ * stream rules are those of the single-lattice API; the handle owns its
+ * extra streams and events and releases them in wblbe_slabs_destroy. */
 typedef struct wblbe_slabs* wblbe_slabs_handle;
 
 /* First global row of every slab: row_starts[k] for k = 0..nslabs
@@ -368,7 +372,8 @@ size_t wblbe_slabs_workspace_bytes(const wblbe_params* params, int32_t nslabs);
 
 /* Create a split lattice (workspace borrowed until destroy).  EINVAL on
  * bad parameters, scheme 4, too many slabs or a short/misaligned workspace
- * (ENOMEM when only short). */
+ * (ENOMEM when only short); ECUDA if its streams or events cannot be
+ * created.  Synchronous (uploads the exchange table). */
 wblbe_status wblbe_slabs_create(const wblbe_params* params, int32_t nslabs,
                                 void* dev_workspace, size_t workspace_bytes,
                                 void* cuda_stream, wblbe_slabs_handle* out);
