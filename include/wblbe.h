@@ -86,12 +86,16 @@ enum { WBLBE_STANDARD = 0, WBLBE_WELL_BALANCED = 1, WBLBE_STANDARD_PRESSURE = 2,
  *   (standard: s_i = w_i rho_ref; well-balanced: s_0 = rho_ref - (1-w_0) rho0,
  *   s_i = w_i rho0), arithmetic in float32, reductions in float64.  The shift
  *   is exact in real arithmetic: sum_i s_i = rho_ref and a uniform s_i is
- *   invariant under streaming.  Near a steady state the float32 rounding
- *   repeats from step to step, so its small biases add up: the mass drifts
- *   (about 1e-4 relative per 1e5 steps on a 256^2 droplet), interfaces drift,
- *   and max|u| settles near 1e-6.  Bulk densities and the Laplace jump stay
- *   close to FP64 (1e-5, 0.3 %).  Equilibria at round-off velocity need
- *   WBLBE_FP64. */
+ *   invariant under streaming.  In the well-balanced scheme the rest
+ *   population is taken from the node's exact mass balance and rounded
+ *   stochastically (zero-mean rounding whose random bits come from a
+ *   counter-based hash of the node and the time step, so results do not
+ *   depend on the launch shape, batching or a slab split; see
+ *   wblbe_set_step_count).  After 1e5 steps of a 256^2 droplet the mass is
+ *   within about 1e-8 of its start, the droplet within 1e-4 lattice units of
+ *   the FP64 run's position, the bulk densities within 1e-6 and the Laplace
+ *   jump within 1e-4 of FP64, and max|u| near 1e-8.  Equilibria at
+ *   round-off velocity need WBLBE_FP64. */
 enum { WBLBE_FP64 = 0, WBLBE_FP32_SHIFTED = 1 };
 
 /* The paper's statement of the problem (Sec. IV): lattice nx x ny (periodic),
