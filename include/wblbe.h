@@ -225,11 +225,14 @@ size_t wblbe_sequence_scratch_bytes(const wblbe_params* params);
  * rho_in, rho_out: n host pointers to [ny][nx] float64 fields (the same
  * pointer may repeat; rho_out[k] is written when the call returns).
  * scratch: caller-owned device memory of wblbe_sequence_scratch_bytes()
- * bytes, 256-byte aligned, not in use by other work.  Synchronises; the
- * handle then holds the last state (its mass reference that state's
- * initial mass).  EINVAL: NULL handle or pointer, n < 0, nsteps < 0, short
- * or misaligned scratch; ECUDA: a failed launch or copy (states before it
- * are complete). */
+ * bytes, 256-byte aligned, not in use by other work.  The call creates two
+ * streams, eight events and a page-locked host buffer of 96 bytes per state
+ * (the statistics records) and releases them before it returns.
+ * Synchronises; the handle then holds the last state (its mass reference
+ * that state's initial mass).  EINVAL: NULL handle or pointer, n < 0,
+ * nsteps < 0, short or misaligned scratch; ECUDA: a failed launch, copy or
+ * stream/event creation (work already issued is drained first; rho_out and
+ * stats are then incomplete). */
 wblbe_status wblbe_run_sequence(wblbe_handle h, int32_t n, const double* const* rho_in,
                                 int64_t nsteps, double* const* rho_out, wblbe_stats* stats,
                                 void* scratch, size_t scratch_bytes);
