@@ -467,9 +467,8 @@ const char* wblbe3_last_error(wblbe3_handle h);
  * 4096 x 4096 needs 65536; 1024 x 1024 needs 4096) are rejected with
  * WBLBE_ENOMEM.  The first call on a device looks up that device's address
  * of the array (cudaGetSymbolAddress).  All calls share the one array:
- * calls that overlap on the
- * GPU (different streams, or different host threads on one device) race and
- * must be serialised by the caller.  Work is issued on cuda_stream (NULL =
+ * calls that overlap on the GPU (different streams, or different host
+ * threads on one device) race and must be serialised by the caller.  Work is issued on cuda_stream (NULL =
  * legacy default stream); when stats is not NULL the call synchronises that
  * stream.  Errors: EINVAL (NULL params/f, invalid parameters, precision not
  * FP64), ENOMEM (lattice too large for the scratch), ECUDA.  The message of
