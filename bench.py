@@ -765,16 +765,21 @@ def run_ours(args, world, rank, local):
                          "unit": "GB/s", "frac": r50["achieved_gbs"] / hbm_peak,
                          "peak_source": peak_note, "kernel_ms": r50["kern_avg"] * 1e3},
             "gpu_launches": r50["launches"], "clocks": r50["clocks"]}
-    if not args.no_schemes:
+    # the one-GPU legs: measured by an N = 1 run only (under torchrun the
+    # other ranks have finished, and their GPUs would wait for rank 0)
+    solo = world == 1
+    if solo and not args.no_schemes:
         line["schemes"] = run_schemes(args, stream, torch)
-    if not args.no_d3q19:
+    if solo and not args.no_d3q19:
         line["d3q19"] = run_d3q19(args, stream, torch, fp64_peak)
-    if not args.no_slabs:
+    if solo and not args.no_slabs:
         line["slabs"] = run_slabs(args, stream, torch, r32["kern_mlups"])
-    if not args.no_batched:
+    if solo and not args.no_batched:
         line["batched"] = run_batched(args, stream, torch)
         if not args.no_serving:
             line["serving"] = run_serving(args, stream, torch, line["batched"]["config"])
+    if not solo:
+        line["one_gpu_legs"] = "measured at n_gpus = 1 only"
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_sample(pr)
     print(json.dumps(line), flush=True)
