@@ -559,13 +559,14 @@ def run_schemes(args, stream, torch):
 
 
 def run_d3q19(args, stream, torch, fp64_peak=None):
-    """The three-dimensional (D3Q19, FP64) well-balanced path: a periodic
-    n^3 lattice with one droplet of radius n/4 (rho_l = 1, rho_g = 0.1,
+    """The three-dimensional (D3Q19) well-balanced path: a periodic n^3
+    lattice with one droplet of radius n/4 (rho_l = 1, rho_g = 0.1,
     kappa = 0.01, W = 4, tau = 1.0); K benchmark steps of S lattice steps,
-    timed by CUDA events on the launching stream.  Three kernels per step
-    (density, chemical potential, collide-stream); algorithmic bytes per
-    update 304 (19 float64 populations read and written), the kernels move
-    about 496 (the density and chemical-potential fields, and the
+    timed by CUDA events on the launching stream, in FP64 and in
+    FP32-shifted storage.  Three kernels per step (density, chemical
+    potential, collide-stream); algorithmic bytes per update 19 populations
+    read and written (304 in FP64, 152 in FP32); the kernels move about
+    496 / 248 (the density and chemical-potential fields, and the
     populations read twice)."""
     from paper_2012_11075_gb300 import wblbe
     from paper_2012_11075_gb300 import workloads as wl
@@ -574,30 +575,37 @@ def run_d3q19(args, stream, torch, fp64_peak=None):
     r = np.sqrt((x - n // 2) ** 2 + (y - n // 2) ** 2 + (z - n // 2) ** 2)
     rho = 0.55 - 0.45 * np.tanh(2 * (r - n / 4) / 4.0)
     beta = wl.beta_for_width(0.01, 4.0, 1.0, 0.1)
-    s = wblbe.Solver3(wblbe.Params3(n, n, n, 1.0, 0.01, beta, 1.0, 0.1), stream=stream)
-    s.init_rho(rho)
-    S, K = 20, max(1, min(args.steps, 5))
-    for _ in range(2):
-        s.step(S)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    l0 = s.kernel_launches
-    with torch.cuda.stream(stream):
-        ev[0].record(stream)
-        s.step(S * K)
-        ev[1].record(stream)
-    torch.cuda.synchronize()
-    dt = ev[0].elapsed_time(ev[1]) / 1e3
-    st = s.stats()
-    launches = s.kernel_launches - l0
-    s.close()
-    lups = n ** 3 * S * K / dt
     peak = measured_peaks().get("hbm_gbs") or 6800.0
+
+    def timed(precision):
+        s = wblbe.Solver3(wblbe.Params3(n, n, n, 1.0, 0.01, beta, 1.0, 0.1, 0.0,
+                                        wblbe.WELL_BALANCED, precision), stream=stream)
+        s.init_rho(rho)
+        S = 20 if precision == wblbe.FP64 else 100
+        K = max(1, min(args.steps, 5))
+        for _ in range(2):
+            s.step(S)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        l0 = s.kernel_launches
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            s.step(S * K)
+            ev[1].record(stream)
+        torch.cuda.synchronize()
+        dt = ev[0].elapsed_time(ev[1]) / 1e3
+        st = s.stats()
+        launches = s.kernel_launches - l0
+        s.close()
+        return n ** 3 * S * K / dt, S * K, dt, launches, st
+
+    lups, steps, dt, launches, st = timed(wblbe.FP64)
     if fp64_peak is None:
         fp64_peak = measure_fp64_peak(stream, torch)
     alu = lups * D3_FLOPS_PER_LU / 1e12
+    l32, steps32, dt32, launches32, st32 = timed(wblbe.FP32_SHIFTED)
     return {"workload": f"d3q19_{n}^3_droplet_wb_fp64", "value": lups / 1e6, "unit": UNIT,
-            "lattice_steps": S * K, "seconds": dt, "gpu_launches": launches,
+            "lattice_steps": steps, "seconds": dt, "gpu_launches": launches,
             "bytes_per_lattice_update": 304,
             "hbm_frac_algorithmic": 304 * lups / 1e9 / peak,
             "hbm_frac_moved": 496 * lups / 1e9 / peak,
@@ -607,7 +615,16 @@ def run_d3q19(args, stream, torch, fp64_peak=None):
                              "flops_per_lattice_update": D3_FLOPS_PER_LU,
                              "peak_source": "of measured (FP64 FMA probe kernel, this run)"},
             "umax": st["umax"], "mass_drift_rel": st["mass_drift_rel"],
-            "nonfinite": bool(st["nonfinite"])}
+            "nonfinite": bool(st["nonfinite"]),
+            "fp32": {"workload": f"d3q19_{n}^3_droplet_wb_fp32_shifted", "value": l32 / 1e6,
+                     "unit": UNIT, "lattice_steps": steps32, "seconds": dt32,
+                     "gpu_launches": launches32, "bytes_per_lattice_update": 152,
+                     "roofline": {"bound": "hbm", "achieved": 152 * l32 / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": 152 * l32 / 1e9 / peak,
+                                  "peak_source": "of measured"},
+                     "hbm_frac_moved": 248 * l32 / 1e9 / peak,
+                     "umax": st32["umax"], "mass_drift_rel": st32["mass_drift_rel"],
+                     "nonfinite": bool(st32["nonfinite"])}}
 
 
 def run_ours(args, world, rank, local):

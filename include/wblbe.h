@@ -418,7 +418,13 @@ const char* wblbe_slabs_last_error(wblbe_slabs_handle h);
  *   c7..c18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
  *             (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
  * Scalar fields are [nz][ny][nx] float64 (x fastest); u is [3][nz][ny][nx];
- * populations [19][nz][ny][nx].  Conventions as for the 2D API. */
+ * populations [19][nz][ny][nx].  Conventions as for the 2D API.
+ * WBLBE_FP32_SHIFTED stores float32 deviations g_i = f_i - s_i from the
+ * scheme's rest equilibrium at rho_ref = rho_g (and the well-balanced rho0
+ * vector), with float32 arithmetic and float64 reductions; in the
+ * well-balanced scheme the rest population comes from the exact node mass
+ * balance and is rounded stochastically, one draw per node from a hash of
+ * the node and the step, as in 2D. */
 typedef struct wblbe3_ctx* wblbe3_handle;
 
 typedef struct {
@@ -426,6 +432,7 @@ typedef struct {
   double tau, kappa, beta, rho_l, rho_g;
   double rho0;                     /* Eq. mFeq; well-balanced scheme only  */
   int32_t scheme;                  /* WBLBE_STANDARD | WBLBE_WELL_BALANCED */
+  int32_t precision;               /* WBLBE_FP64 | WBLBE_FP32_SHIFTED      */
 } wblbe3_params;
 
 /* Workspace bytes (0 on invalid parameters): two population buffers, the

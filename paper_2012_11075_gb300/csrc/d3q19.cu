@@ -62,7 +62,41 @@ struct P3 {
   int nx, ny, nz, pitch;
   long long plane;                 // elements per population plane / field
   double omega, kforce, kappa, two_beta, rho_l, rho_g;
+  // storage shift density (0 in FP64) and rho_ref - rho_l, rho_ref - rho_g
+  double rho_ref, dl, dg;
+  long long step;                  // the step being taken (FP32 rounding draws)
 };
+
+// Mirror-symmetric sum of the eighteen moving populations: opposite pairs
+// first, the axis pairs together and the edge pairs by plane, so that a
+// reflection of any axis maps the grouping onto itself (mirror-image nodes
+// round alike; the FP32 path).
+template <typename T>
+__device__ __forceinline__ T moving_sum3(const T (&g)[19]) {
+  const T ax = ((g[1] + g[2]) + (g[3] + g[4])) + (g[5] + g[6]);
+  const T xy = (g[7] + g[8]) + (g[9] + g[10]);
+  const T xz = (g[11] + g[12]) + (g[13] + g[14]);
+  const T yz = (g[15] + g[16]) + (g[17] + g[18]);
+  return ax + ((xy + xz) + yz);
+}
+
+// Single-node forms of the FP32 exact-mass rounding of the 2D kernel:
+// TwoSum (Knuth), a uniform draw in [0, 1) on a 2^-23 grid from the node key
+// k and the step key ht (MurmurHash3's finalizer), and the stochastic
+// rounding of h + e to h or its neighbour on the side of e with probability
+// |e| / gap.
+__device__ __forceinline__ void two_sum1(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+__device__ __forceinline__ float node_uniform(uint32_t k, uint32_t ht) {
+  return __fsub_rn(__uint_as_float(0x3f800000u | (fmix32(k + ht) >> 9)), 1.0f);
+}
+__device__ __forceinline__ float round_stochastic1(float h, float e, float u) {
+  const float n = next_toward(h, e);
+  return fabsf(__fmul_rn(u, __fsub_rn(n, h))) < fabsf(e) ? n : h;
+}
 
 struct Out3 {
   double* rho;                     // [nz][ny][nx] fields (may be null)
@@ -79,59 +113,76 @@ __device__ __forceinline__ long long at3(const P3& p, int x, int y, int z) {
   return ((long long)z * p.ny + y) * p.pitch + x;
 }
 
-// rho = sum_i f_i with f_i(x) = P_i(x - c_i), summed from i = 0 to 18.
-__global__ void __launch_bounds__(kBlock3) d3_density(const double* __restrict__ src,
-                                                      double* __restrict__ rho, const P3 p) {
+// rho = sum_i f_i with f_i(x) = P_i(x - c_i): in FP64 summed from i = 0 to
+// 18; in FP32 the stored deviation rs = rho - rho_ref = g_0 + the
+// mirror-symmetric moving sum (the collision repeats that sum for the exact
+// mass balance).
+template <typename T>
+__global__ void __launch_bounds__(kBlock3) d3_density(const T* __restrict__ src,
+                                                      T* __restrict__ rho, const P3 p) {
   const int x = blockIdx.x * kBlock3 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= p.nx) return;
-  double s = src[at3(p, x, y, z)];              // f_0 (c_0 = 0)
+  if (sizeof(T) == 8) {
+    T s = src[at3(p, x, y, z)];                   // f_0 (c_0 = 0)
 #pragma unroll
-  for (int i = 1; i < kQ3; ++i)
-    s += src[i * p.plane + at3(p, wrap3(x - cx3(i), p.nx), wrap3(y - cy3(i), p.ny),
-                               wrap3(z - cz3(i), p.nz))];
-  rho[at3(p, x, y, z)] = s;
+    for (int i = 1; i < kQ3; ++i)
+      s += src[i * p.plane + at3(p, wrap3(x - cx3(i), p.nx), wrap3(y - cy3(i), p.ny),
+                                 wrap3(z - cz3(i), p.nz))];
+    rho[at3(p, x, y, z)] = s;
+  } else {
+    T g[kQ3];
+#pragma unroll
+    for (int i = 0; i < kQ3; ++i)
+      g[i] = src[i * p.plane + at3(p, wrap3(x - cx3(i), p.nx), wrap3(y - cy3(i), p.ny),
+                                   wrap3(z - cz3(i), p.nz))];
+    rho[at3(p, x, y, z)] = g[0] + moving_sum3(g);
+  }
 }
 
 // mu = mu_0(rho) - kappa lap(rho), mu_0 = 2 beta a b (a + b), a = rho - rho_l,
 // b = rho - rho_g (Eq. doubleWell), lap = 6 sum_i w_i (rho(x + c_i) - rho(x)).
-__global__ void __launch_bounds__(kBlock3) d3_chem_pot(const double* __restrict__ rho,
-                                                       double* __restrict__ mu, const P3 p) {
+// The field holds rho - rho_ref (rho_ref = 0 in FP64), which the Laplacian
+// does not see and a, b take up through dl = rho_ref - rho_l, dg.
+template <typename T>
+__global__ void __launch_bounds__(kBlock3) d3_chem_pot(const T* __restrict__ rho,
+                                                       T* __restrict__ mu, const P3 p) {
   const int x = blockIdx.x * kBlock3 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= p.nx) return;
-  const double c = rho[at3(p, x, y, z)];
+  const T c = rho[at3(p, x, y, z)];
   // sums of the axis and edge neighbours, then the centre's share taken off
   // once per sum (rather than from every neighbour): 6 (ax/18 + ed/36)
   auto nbr = [&](int i) {
     return __ldg(rho + at3(p, wrap3(x + cx3(i), p.nx), wrap3(y + cy3(i), p.ny),
                            wrap3(z + cz3(i), p.nz)));
   };
-  double ax = nbr(1), ed = nbr(7);
+  T ax = nbr(1), ed = nbr(7);
 #pragma unroll
   for (int i = 2; i < kQ3; ++i) {
     if (i == 7) continue;
     if (i < 7) ax += nbr(i); else ed += nbr(i);
   }
-  const double lap = (1.0 / 3.0) * (ax - 6.0 * c) + (1.0 / 6.0) * (ed - 12.0 * c);
-  const double a = c - p.rho_l, b = c - p.rho_g;
-  mu[at3(p, x, y, z)] = p.two_beta * a * b * (a + b) - p.kappa * lap;
+  const T lap = T(1.0 / 3.0) * (ax - T(6) * c) + T(1.0 / 6.0) * (ed - T(12) * c);
+  const T a = c + T(p.dl), b = c + T(p.dg);
+  mu[at3(p, x, y, z)] = T(p.two_beta) * a * b * (a + b) - T(p.kappa) * lap;
 }
 
 // 12 grad(phi) = 36 sum_i w_i c_i phi(x + c_i): 2 (axis differences) +
 // (edge differences); the factor 1/12 is folded into the constants that
 // use the gradients.
-__device__ __forceinline__ void grad3x12(const double* __restrict__ phi, const P3& p, int x,
-                                         int y, int z, double& gx, double& gy, double& gz) {
+template <typename T>
+__device__ __forceinline__ void grad3x12(const T* __restrict__ phi, const P3& p, int x, int y,
+                                         int z, T& gx, T& gy, T& gz) {
   auto v = [&](int dx, int dy, int dz) {
     return __ldg(phi + at3(p, wrap3(x + dx, p.nx), wrap3(y + dy, p.ny), wrap3(z + dz, p.nz)));
   };
-  const double axx = v(1, 0, 0) - v(-1, 0, 0), axy = v(0, 1, 0) - v(0, -1, 0),
-               axz = v(0, 0, 1) - v(0, 0, -1);
-  const double exy1 = v(1, 1, 0) - v(-1, -1, 0), exy2 = v(1, -1, 0) - v(-1, 1, 0);
-  const double exz1 = v(1, 0, 1) - v(-1, 0, -1), exz2 = v(1, 0, -1) - v(-1, 0, 1);
-  const double eyz1 = v(0, 1, 1) - v(0, -1, -1), eyz2 = v(0, 1, -1) - v(0, -1, 1);
-  gx = 2.0 * axx + ((exy1 + exy2) + (exz1 + exz2));
-  gy = 2.0 * axy + ((exy1 - exy2) + (eyz1 + eyz2));
-  gz = 2.0 * axz + ((exz1 - exz2) + (eyz1 - eyz2));
+  const T axx = v(1, 0, 0) - v(-1, 0, 0), axy = v(0, 1, 0) - v(0, -1, 0),
+          axz = v(0, 0, 1) - v(0, 0, -1);
+  const T exy1 = v(1, 1, 0) - v(-1, -1, 0), exy2 = v(1, -1, 0) - v(-1, 1, 0);
+  const T exz1 = v(1, 0, 1) - v(-1, 0, -1), exz2 = v(1, 0, -1) - v(-1, 0, 1);
+  const T eyz1 = v(0, 1, 1) - v(0, -1, -1), eyz2 = v(0, 1, -1) - v(0, -1, 1);
+  gx = T(2) * axx + ((exy1 + exy2) + (exz1 + exz2));
+  gy = T(2) * axy + ((exy1 - exy2) + (eyz1 + eyz2));
+  gz = T(2) * axz + ((exz1 - exz2) + (eyz1 - eyz2));
 }
 
 // The collision of one node, and its stores (MOMENTS: fields and stats
@@ -144,111 +195,148 @@ __device__ __forceinline__ void grad3x12(const double* __restrict__ phi, const P
 //   t = -3/2 omega rho u.u - 3 kforce u.G,
 // G = F + cs^2 grad rho and h = (3|c|^2 - 3)/2 (Eq. mFi, D = 3) for the
 // well-balanced scheme, G = F and h = 0 for the standard one (Eq. Fi).
-template <bool WB, bool MOMENTS>
-__global__ void __launch_bounds__(kBlock3) d3_collide(const double* __restrict__ src,
-                                                      double* __restrict__ dst,
-                                                      const double* __restrict__ rho,
-                                                      const double* __restrict__ mu,
+template <typename T, bool WB, bool MOMENTS>
+__global__ void __launch_bounds__(kBlock3) d3_collide(const T* __restrict__ src,
+                                                      T* __restrict__ dst,
+                                                      const T* __restrict__ rho,
+                                                      const T* __restrict__ mu,
                                                       const P3 p, const Out3 out) {
+  constexpr bool kShifted = sizeof(T) == 4;    // FP32 stores g_i = f_i - s_i
   const int x = blockIdx.x * kBlock3 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   const bool own = x < p.nx;
   double st[kStatRec] = {0.0, 0.0, 0.0, 1e300, -1e300, 0.0};
   if (own) {
-    double g[kQ3];
+    T g[kQ3];
 #pragma unroll
     for (int i = 0; i < kQ3; ++i)
       g[i] = src[i * p.plane + at3(p, wrap3(x - cx3(i), p.nx), wrap3(y - cy3(i), p.ny),
                                    wrap3(z - cz3(i), p.nz))];
     const long long k = at3(p, x, y, z);
-    const double r = rho[k];
+    const T rs = rho[k];                         // rho - rho_ref (rho in FP64)
+    const T r = kShifted ? rs + T(p.rho_ref) : rs;
     // 12 grad mu, 12 grad rho; F = -rho grad mu (Eq. mF), or the potential
     // form cs^2 grad rho - rho grad mu of the standard scheme
-    double gmx, gmy, gmz, grx, gry, grz;
-    grad3x12(mu, p, x, y, z, gmx, gmy, gmz);
-    grad3x12(rho, p, x, y, z, grx, gry, grz);
-    const double nr = r * (-1.0 / 12.0);
-    double Fx, Fy, Fz;
+    T gmx, gmy, gmz, grx, gry, grz;
+    grad3x12<T>(mu, p, x, y, z, gmx, gmy, gmz);
+    grad3x12<T>(rho, p, x, y, z, grx, gry, grz);
+    const T nr = r * T(-1.0 / 12.0);
+    T Fx, Fy, Fz;
     if (WB) {
       Fx = nr * gmx;
       Fy = nr * gmy;
       Fz = nr * gmz;
     } else {
-      Fx = (1.0 / 36.0) * grx + nr * gmx;
-      Fy = (1.0 / 36.0) * gry + nr * gmy;
-      Fz = (1.0 / 36.0) * grz + nr * gmz;
+      Fx = T(1.0 / 36.0) * grx + nr * gmx;
+      Fy = T(1.0 / 36.0) * gry + nr * gmy;
+      Fz = T(1.0 / 36.0) * grz + nr * gmz;
     }
     // momentum from the differences of opposite pairs (each edge difference
     // serves two components)
-    const double d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
-    const double d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
-    const double d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
-    const double jx = ((d12 + d78) + (d910 + d1112)) + d1314;
-    const double jy = ((d34 + d78) - (d910 - d1516)) + d1718;
-    const double jz = ((d56 + d1112) - (d1314 - d1516)) - d1718;
-    const double inv = recip(r);
-    const double ux = (jx + 0.5 * Fx) * inv, uy = (jy + 0.5 * Fy) * inv,
-                 uz = (jz + 0.5 * Fz) * inv;                     // Eq. rhoU
-    const double muc = mu[k];
+    const T d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
+    const T d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
+    const T d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
+    const T jx = ((d12 + d78) + (d910 + d1112)) + d1314;
+    const T jy = ((d34 + d78) - (d910 - d1516)) + d1718;
+    const T jz = ((d56 + d1112) - (d1314 - d1516)) - d1718;
+    const T inv = recip(r);
+    const T ux = (jx + T(0.5) * Fx) * inv, uy = (jy + T(0.5) * Fy) * inv,
+            uz = (jz + T(0.5) * Fz) * inv;                       // Eq. rhoU
+    const T muc = mu[k];
     if (MOMENTS) {
-      if (out.rho) out.rho[(size_t)(z * p.ny + y) * p.nx + x] = r;
-      if (out.ux) out.ux[(size_t)(z * p.ny + y) * p.nx + x] = ux;
-      if (out.uy) out.uy[(size_t)(z * p.ny + y) * p.nx + x] = uy;
-      if (out.uz) out.uz[(size_t)(z * p.ny + y) * p.nx + x] = uz;
-      if (out.mu) out.mu[(size_t)(z * p.ny + y) * p.nx + x] = muc;
-      const double u2 = ux * ux + uy * uy + uz * uz;
-      st[0] = r;
-      st[1] = 0.5 * r * u2;
+      const double rd = kShifted ? (double)rs + p.rho_ref : (double)r;
+      const double uxd = ux, uyd = uy, uzd = uz, mud = muc;
+      if (out.rho) out.rho[(size_t)(z * p.ny + y) * p.nx + x] = rd;
+      if (out.ux) out.ux[(size_t)(z * p.ny + y) * p.nx + x] = uxd;
+      if (out.uy) out.uy[(size_t)(z * p.ny + y) * p.nx + x] = uyd;
+      if (out.uz) out.uz[(size_t)(z * p.ny + y) * p.nx + x] = uzd;
+      if (out.mu) out.mu[(size_t)(z * p.ny + y) * p.nx + x] = mud;
+      const double u2 = uxd * uxd + uyd * uyd + uzd * uzd;
+      st[0] = rd;
+      st[1] = 0.5 * rd * u2;
       st[2] = u2;
-      st[3] = muc;
-      st[4] = muc;
-      st[5] = (!isfinite(r) || !isfinite(muc) || !isfinite(u2)) ? 1.0 : 0.0;
+      st[3] = mud;
+      st[4] = mud;
+      st[5] = (!isfinite(rd) || !isfinite(mud) || !isfinite(u2)) ? 1.0 : 0.0;
     } else {
-      const double om = p.omega, kf = p.kforce;
-      const double keep = 1.0 - om;
-      double Gx = Fx, Gy = Fy, Gz = Fz;
-      if (WB) {
-        Gx = Fx + (1.0 / 36.0) * grx;                           // G = F + cs^2 grad rho
-        Gy = Fy + (1.0 / 36.0) * gry;
-        Gz = Fz + (1.0 / 36.0) * grz;
+      T om = T(p.omega);
+      const T kf = T(p.kforce);
+      T keep = T(1) - om;
+      if (kShifted && om < T(0.5)) {
+        // keep + omega == 1 exactly in float (the update then conserves
+        // mass); 1 - omega is exact by Sterbenz only for omega >= 1/2
+        keep = T(1.0 - p.omega);
+        om = T(1) - keep;
       }
-      const double orho = om * r;
-      const double t = -1.5 * orho * (ux * ux + uy * uy + uz * uz) -
-                       3.0 * kf * (ux * Gx + uy * Gy + uz * Gz);
-      const double ku = WB ? (kf * (1.0 / 12.0)) * (ux * grx + uy * gry + uz * grz) : 0.0;
+      // FP32: the moving populations' sum before the collision (the same
+      // grouping as the density), for the exact node mass balance below
+      const T m_in = kShifted ? moving_sum3(g) : T(0);
+      T Gx = Fx, Gy = Fy, Gz = Fz;
+      if (WB) {
+        Gx = Fx + T(1.0 / 36.0) * grx;                          // G = F + cs^2 grad rho
+        Gy = Fy + T(1.0 / 36.0) * gry;
+        Gz = Fz + T(1.0 / 36.0) * grz;
+      }
+      const T orho = om * r;
+      const T obase = om * rs;                   // omega (rho - rho_ref): the stored base
+      const T t = T(-1.5) * orho * (ux * ux + uy * uy + uz * uz) -
+                  T(3.0) * kf * (ux * Gx + uy * Gy + uz * Gz);
+      const T ku = WB ? (kf * T(1.0 / 12.0)) * (ux * grx + uy * gry + uz * grz) : T(0);
       // per-node constants of the pairs, with the weights folded in
       // (w_ax = 1/18, w_edge = 1/36): E = C + cu (A cu + K.c), O = 3 w c.M
-      const double Ca = WB ? (1.0 / 18.0) * t : (1.0 / 18.0) * (t + orho);
-      const double Ce = WB ? (1.0 / 36.0) * (t + 1.5 * ku) : (1.0 / 36.0) * (t + orho);
-      const double Aa = 0.25 * orho, Ae = 0.125 * orho;          // w 9/2 omega rho
-      const double kh = 0.5 * kf, kq = 0.25 * kf, k6 = kf * (1.0 / 6.0);
-      const double Kax = kh * Gx, Kay = kh * Gy, Kaz = kh * Gz;  // 9 w_ax kforce G
-      const double Kex = kq * Gx, Key = kq * Gy, Kez = kq * Gz;  // 9 w_edge kforce G
-      const double o6 = orho * (1.0 / 6.0);                      // 3 w_ax (omega rho u + kforce F)
-      const double Mx = o6 * ux + k6 * Fx, My = o6 * uy + k6 * Fy, Mz = o6 * uz + k6 * Fz;
-      auto axis = [&](int i, int j, double cu, double K, double M) {
-        const double E = Ca + cu * (Aa * cu + K);
+      const T Ca = WB ? T(1.0 / 18.0) * t : T(1.0 / 18.0) * (t + obase);
+      const T Ce = WB ? T(1.0 / 36.0) * (t + T(1.5) * ku) : T(1.0 / 36.0) * (t + obase);
+      const T Aa = T(0.25) * orho, Ae = T(0.125) * orho;         // w 9/2 omega rho
+      const T kh = T(0.5) * kf, kq = T(0.25) * kf, k6 = kf * T(1.0 / 6.0);
+      const T Kax = kh * Gx, Kay = kh * Gy, Kaz = kh * Gz;       // 9 w_ax kforce G
+      const T Kex = kq * Gx, Key = kq * Gy, Kez = kq * Gz;       // 9 w_edge kforce G
+      const T o6 = orho * T(1.0 / 6.0);                          // 3 w_ax (omega rho u + kforce F)
+      const T Mx = o6 * ux + k6 * Fx, My = o6 * uy + k6 * Fy, Mz = o6 * uz + k6 * Fz;
+      auto axis = [&](int i, int j, T cu, T K, T M) {
+        const T E = Ca + cu * (Aa * cu + K);
         g[i] = keep * g[i] + (E + M);
         g[j] = keep * g[j] + (E - M);
+        return E;
       };
       // edge pair: 3 w_edge c.M = (Ma + Mb) / 2 for c = a + b
-      auto edge = [&](int i, int j, double cu, double K, double S) {
-        const double E = Ce + cu * (Ae * cu + K);
-        g[i] = keep * g[i] + (E + 0.5 * S);
-        g[j] = keep * g[j] + (E - 0.5 * S);
+      auto edge = [&](int i, int j, T cu, T K, T S) {
+        const T E = Ce + cu * (Ae * cu + K);
+        g[i] = keep * g[i] + (E + T(0.5) * S);
+        g[j] = keep * g[j] + (E - T(0.5) * S);
+        return E;
       };
-      axis(1, 2, ux, Kax, Mx);
-      axis(3, 4, uy, Kay, My);
-      axis(5, 6, uz, Kaz, Mz);
-      edge(7, 8, ux + uy, Kex + Key, Mx + My);
-      edge(9, 10, ux - uy, Kex - Key, Mx - My);
-      edge(11, 12, ux + uz, Kex + Kez, Mx + Mz);
-      edge(13, 14, ux - uz, Kex - Kez, Mx - Mz);
-      edge(15, 16, uy + uz, Key + Kez, My + Mz);
-      edge(17, 18, uy - uz, Key - Kez, My - Mz);
-      // rest: WB f_0^eq - s_0 = rho - w_0 3/2 rho u.u, F_0 = w_0 (-3 u.G - 3/2 u.grad rho);
-      // standard f_0^eq = w_0 rho (1 - 3/2 u.u), F_0 = w_0 (-3 u.G)
-      const double w0 = 1.0 / 3.0;
-      g[0] = keep * g[0] + (WB ? orho + w0 * (t - 1.5 * ku) : w0 * (t + orho));
+      const T Ea1 = axis(1, 2, ux, Kax, Mx);
+      const T Ea2 = axis(3, 4, uy, Kay, My);
+      const T Ea3 = axis(5, 6, uz, Kaz, Mz);
+      const T Ee1 = edge(7, 8, ux + uy, Kex + Key, Mx + My);
+      const T Ee2 = edge(9, 10, ux - uy, Kex - Key, Mx - My);
+      const T Ee3 = edge(11, 12, ux + uz, Kex + Kez, Mx + Mz);
+      const T Ee4 = edge(13, 14, ux - uz, Kex - Kez, Mx - Mz);
+      const T Ee5 = edge(15, 16, uy + uz, Key + Kez, My + Mz);
+      const T Ee6 = edge(17, 18, uy - uz, Key - Kez, My - Mz);
+      if constexpr (kShifted) {
+        if (WB) {
+          // The collision conserves the node's mass, so the rest population
+          // follows from the balance: g_0' = g_0 + omega m_in - 2 sum E (the
+          // moving ones leave as keep g + E +- O).  Its small one-signed
+          // O(u^2) part would be lost in rounding g_0 ~ rho - rho_ref to
+          // float; TwoSum keeps the remainder and a zero-mean rounding,
+          // seeded by the node and the step, takes it into account.
+          const T sE = ((Ea1 + Ea2) + Ea3) + (((Ee1 + Ee2) + (Ee3 + Ee4)) + (Ee5 + Ee6));
+          T hsum, err;
+          two_sum1(g[0], __fmaf_rn(-2.0f, sE, om * m_in), hsum, err);
+          const uint32_t key = (uint32_t)(((long long)z * p.ny + y) * p.nx + x);
+          g[0] = round_stochastic1(hsum, err, node_uniform(key, step_key(p.step)));
+        } else {
+          g[0] = rs - moving_sum3(g);          // the standard scheme: the mass balance
+        }
+      } else {
+        (void)Ea1; (void)Ea2; (void)Ea3; (void)Ee1; (void)Ee2; (void)Ee3;
+        (void)Ee4; (void)Ee5; (void)Ee6; (void)m_in;
+        // rest: WB f_0^eq - s_0 = rho - w_0 3/2 rho u.u, F_0 = w_0 (-3 u.G - 3/2 u.grad rho);
+        // standard f_0^eq = w_0 rho (1 - 3/2 u.u), F_0 = w_0 (-3 u.G)
+        const T w0 = T(1.0 / 3.0);
+        g[0] = keep * g[0] + (WB ? obase + w0 * (t - T(1.5) * ku) : w0 * (t + obase));
+      }
 #pragma unroll
       for (int i = 0; i < kQ3; ++i) dst[i * p.plane + k] = g[i];
     }
@@ -296,7 +384,8 @@ __global__ void __launch_bounds__(kBlock3) d3_collide(const double* __restrict__
 }
 
 // f = f^eq(rho, 0) stored for the pull: P_i(x) = f_i^eq(rho(x + c_i)) - s_i.
-__global__ void d3_init(const double* __restrict__ rho_in, double* __restrict__ dst, const P3 p,
+template <typename T>
+__global__ void d3_init(const double* __restrict__ rho_in, T* __restrict__ dst, const P3 p,
                         int wb) {
   const int x = blockIdx.x * kBlock3 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= p.nx) return;
@@ -304,19 +393,21 @@ __global__ void d3_init(const double* __restrict__ rho_in, double* __restrict__ 
   for (int i = 0; i < kQ3; ++i) {
     const int xx = wrap3(x + cx3(i), p.nx), yy = wrap3(y + cy3(i), p.ny),
               zz = wrap3(z + cz3(i), p.nz);
-    const double r = rho_in[(size_t)(zz * p.ny + yy) * p.nx + xx];
-    // WB: f_0^eq - s_0 = rho, f_i^eq - s_i = 0; standard: w_i rho
-    dst[i * p.plane + at3(p, x, y, z)] = wb ? (i == 0 ? r : 0.0) : w3(i) * r;
+    const double r = rho_in[(size_t)(zz * p.ny + yy) * p.nx + xx] - p.rho_ref;
+    // WB: f_0^eq - s_0 = rho - rho_ref, f_i^eq - s_i = 0; standard: w_i (rho - rho_ref)
+    dst[i * p.plane + at3(p, x, y, z)] = (T)(wb ? (i == 0 ? r : 0.0) : w3(i) * r);
   }
 }
 
 // f_i(x) = P_i(x - c_i) + s_i for one direction, [nz][ny][nx].
-__global__ void d3_get(const double* __restrict__ src, double* __restrict__ f, const P3 p,
-                       int dir, double shift) {
+template <typename T>
+__global__ void d3_get(const T* __restrict__ src, double* __restrict__ f, const P3 p, int dir,
+                       double shift) {
   const int x = blockIdx.x * kBlock3 + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
   if (x >= p.nx) return;
-  const double v = src[dir * p.plane + at3(p, wrap3(x - cx3(dir), p.nx),
-                                           wrap3(y - cy3(dir), p.ny), wrap3(z - cz3(dir), p.nz))];
+  const double v = (double)src[dir * p.plane + at3(p, wrap3(x - cx3(dir), p.nx),
+                                                   wrap3(y - cy3(dir), p.ny),
+                                                   wrap3(z - cz3(dir), p.nz))];
   f[(size_t)(z * p.ny + y) * p.nx + x] = v + shift;
 }
 
@@ -331,12 +422,14 @@ struct Layout3 {
   long long records;
 };
 
+size_t elem3(const wblbe3_params* p) { return p->precision == WBLBE_FP64 ? 8 : 4; }
+
 Layout3 layout3(const wblbe3_params* p) {
   Layout3 L{};
   L.pitch = (p->nx + 15) / 16 * 16;
   L.plane = (long long)L.pitch * p->ny * p->nz;
-  const size_t pops = align3((size_t)kQ3 * L.plane * sizeof(double));
-  const size_t field = align3((size_t)L.plane * sizeof(double));
+  const size_t pops = align3((size_t)kQ3 * L.plane * elem3(p));
+  const size_t field = align3((size_t)L.plane * elem3(p));
   L.records = (long long)((p->nx + kBlock3 - 1) / kBlock3) * p->ny * p->nz;
   size_t off = 0;
   L.off_a = off; off += pops;
@@ -360,6 +453,9 @@ bool params3_valid(const wblbe3_params* p, char* why, size_t n) {
   if (p->scheme != WBLBE_STANDARD && p->scheme != WBLBE_WELL_BALANCED) {
     snprintf(why, n, "the D3Q19 path runs the standard and well-balanced schemes"); return false;
   }
+  if (p->precision != WBLBE_FP64 && p->precision != WBLBE_FP32_SHIFTED) {
+    snprintf(why, n, "unknown precision %d", p->precision); return false;
+  }
   if ((long long)((p->nx + 15) / 16 * 16) * p->ny * p->nz >= (1LL << 40) ||
       p->ny > 65535 || p->nz > 65535) {
     snprintf(why, n, "lattice too large (ny, nz <= 65535)"); return false;
@@ -374,9 +470,10 @@ struct wblbe3_ctx {
   Layout3 L;
   int device;
   cudaStream_t stream;
-  double* buf[2];
+  void* buf[2];                   // population buffers (float64 or float32)
   int cur;
-  double *rho, *mu, *stage, *partials, *stats;
+  void *rho, *mu;                 // rho - rho_ref and mu fields (the same type)
+  double *stage, *partials, *stats;
   int64_t steps, launches;
   double mass0;
   bool have_state;
@@ -414,6 +511,11 @@ P3 p3_of(const wblbe3_ctx* h) {
   q.two_beta = 2.0 * h->p.beta;
   q.rho_l = h->p.rho_l;
   q.rho_g = h->p.rho_g;
+  // FP32 stores deviations from the rest equilibrium at rho_ref = rho_g
+  q.rho_ref = h->p.precision == WBLBE_FP64 ? 0.0 : h->p.rho_g;
+  q.dl = q.rho_ref - h->p.rho_l;
+  q.dg = q.rho_ref - h->p.rho_g;
+  q.step = h->steps;
   return q;
 }
 
@@ -421,28 +523,41 @@ dim3 grid3(const wblbe3_ctx* h) {
   return dim3((h->p.nx + kBlock3 - 1) / kBlock3, h->p.ny, h->p.nz);
 }
 
+// The stored shift s_i: the well-balanced rho0 vector, plus in FP32 the
+// scheme's rest equilibrium at rho_ref = rho_g.
 double shift3(const wblbe3_params& p, int i) {
-  if (p.scheme != WBLBE_WELL_BALANCED) return 0.0;
-  return i == 0 ? -(1.0 - w3(0)) * p.rho0 : w3(i) * p.rho0;
+  const double rr = p.precision == WBLBE_FP64 ? 0.0 : p.rho_g;
+  if (p.scheme != WBLBE_WELL_BALANCED) return w3(i) * rr;
+  return i == 0 ? rr - (1.0 - w3(0)) * p.rho0 : w3(i) * p.rho0;
 }
 
 // density and chemical potential of the current state, then the collision
 // (step: into the other buffer) or the moments (fields and stats).
+template <typename T>
+void pass3_typed(wblbe3_ctx* h, bool moments, const Out3& out, const P3& q, dim3 g) {
+  const T* src = static_cast<const T*>(h->buf[h->cur]);
+  T* dst = static_cast<T*>(h->buf[1 - h->cur]);
+  T* rho = static_cast<T*>(h->rho);
+  T* mu = static_cast<T*>(h->mu);
+  d3_density<T><<<g, kBlock3, 0, h->stream>>>(src, rho, q);
+  d3_chem_pot<T><<<g, kBlock3, 0, h->stream>>>(rho, mu, q);
+  const bool wb = h->p.scheme == WBLBE_WELL_BALANCED;
+  if (moments) {
+    if (wb) d3_collide<T, true, true><<<g, kBlock3, 0, h->stream>>>(src, nullptr, rho, mu, q, out);
+    else d3_collide<T, false, true><<<g, kBlock3, 0, h->stream>>>(src, nullptr, rho, mu, q, out);
+  } else {
+    if (wb) d3_collide<T, true, false><<<g, kBlock3, 0, h->stream>>>(src, dst, rho, mu, q, out);
+    else d3_collide<T, false, false><<<g, kBlock3, 0, h->stream>>>(src, dst, rho, mu, q, out);
+  }
+}
+
 wblbe_status pass3(wblbe3_ctx* h, bool moments, const Out3& out) {
   const P3 q = p3_of(h);
   const dim3 g = grid3(h);
-  d3_density<<<g, kBlock3, 0, h->stream>>>(h->buf[h->cur], h->rho, q);
-  d3_chem_pot<<<g, kBlock3, 0, h->stream>>>(h->rho, h->mu, q);
-  const bool wb = h->p.scheme == WBLBE_WELL_BALANCED;
-  const double* src = h->buf[h->cur];
-  double* dst = h->buf[1 - h->cur];
-  if (moments) {
-    if (wb) d3_collide<true, true><<<g, kBlock3, 0, h->stream>>>(src, nullptr, h->rho, h->mu, q, out);
-    else d3_collide<false, true><<<g, kBlock3, 0, h->stream>>>(src, nullptr, h->rho, h->mu, q, out);
-  } else {
-    if (wb) d3_collide<true, false><<<g, kBlock3, 0, h->stream>>>(src, dst, h->rho, h->mu, q, out);
-    else d3_collide<false, false><<<g, kBlock3, 0, h->stream>>>(src, dst, h->rho, h->mu, q, out);
-  }
+  if (h->p.precision == WBLBE_FP64)
+    pass3_typed<double>(h, moments, out, q, g);
+  else
+    pass3_typed<float>(h, moments, out, q, g);
   CU3(h, cudaGetLastError());
   h->launches += 3;
   return WBLBE_OK;
@@ -504,10 +619,10 @@ wblbe_status wblbe3_create(const wblbe3_params* params, void* dev_workspace,
   h->p = *params;
   h->L = L;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
-  h->buf[0] = reinterpret_cast<double*>(ws + L.off_a);
-  h->buf[1] = reinterpret_cast<double*>(ws + L.off_b);
-  h->rho = reinterpret_cast<double*>(ws + L.off_rho);
-  h->mu = reinterpret_cast<double*>(ws + L.off_mu);
+  h->buf[0] = ws + L.off_a;
+  h->buf[1] = ws + L.off_b;
+  h->rho = ws + L.off_rho;
+  h->mu = ws + L.off_mu;
   h->stage = reinterpret_cast<double*>(ws + L.off_stage);
   h->partials = reinterpret_cast<double*>(ws + L.off_partials);
   h->stats = reinterpret_cast<double*>(ws + L.off_stats);
@@ -525,8 +640,13 @@ wblbe_status wblbe3_init_rho(wblbe3_handle h, const double* rho, int32_t rho_on_
     src = h->stage;
   }
   h->cur = 0;
-  d3_init<<<grid3(h), kBlock3, 0, h->stream>>>(src, h->buf[0], p3_of(h),
-                                               h->p.scheme == WBLBE_WELL_BALANCED);
+  const int wb = h->p.scheme == WBLBE_WELL_BALANCED;
+  if (h->p.precision == WBLBE_FP64)
+    d3_init<double><<<grid3(h), kBlock3, 0, h->stream>>>(
+        src, static_cast<double*>(h->buf[0]), p3_of(h), wb);
+  else
+    d3_init<float><<<grid3(h), kBlock3, 0, h->stream>>>(
+        src, static_cast<float*>(h->buf[0]), p3_of(h), wb);
   CU3(h, cudaGetLastError());
   h->launches += 1;
   h->steps = 0;
@@ -583,8 +703,12 @@ wblbe_status wblbe3_get_populations(wblbe3_handle h, double* f, int32_t on_devic
   const size_t n = (size_t)h->p.nx * h->p.ny * h->p.nz;
   for (int i = 0; i < kQ3; ++i) {
     double* dst = on_device ? f + i * n : h->stage;
-    d3_get<<<grid3(h), kBlock3, 0, h->stream>>>(h->buf[h->cur], dst, p3_of(h), i,
-                                                shift3(h->p, i));
+    if (h->p.precision == WBLBE_FP64)
+      d3_get<double><<<grid3(h), kBlock3, 0, h->stream>>>(
+          static_cast<const double*>(h->buf[h->cur]), dst, p3_of(h), i, shift3(h->p, i));
+    else
+      d3_get<float><<<grid3(h), kBlock3, 0, h->stream>>>(
+          static_cast<const float*>(h->buf[h->cur]), dst, p3_of(h), i, shift3(h->p, i));
     CU3(h, cudaGetLastError());
     h->launches += 1;
     if (!on_device)

@@ -650,7 +650,7 @@ class CParams3(ctypes.Structure):
                 ("tau", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("beta", ctypes.c_double), ("rho_l", ctypes.c_double),
                 ("rho_g", ctypes.c_double), ("rho0", ctypes.c_double),
-                ("scheme", ctypes.c_int32)]
+                ("scheme", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 # D3Q19 direction order of the wblbe3_* entry points (rest, axes, edges in
@@ -662,8 +662,9 @@ D3Q19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0,
 
 @dataclass
 class Params3:
-    """The three-dimensional (D3Q19, FP64) problem: lattice, tau, the
-    free-energy parameters, rho0 of Eq. mFeq and the scheme."""
+    """The three-dimensional (D3Q19) problem: lattice, tau, the free-energy
+    parameters, rho0 of Eq. mFeq, the scheme and the precision (FP64, or
+    FP32_SHIFTED: float32 deviations from the rest equilibrium at rho_g)."""
     nx: int
     ny: int
     nz: int
@@ -674,14 +675,16 @@ class Params3:
     rho_g: float
     rho0: float = 0.0
     scheme: int = WELL_BALANCED
+    precision: int = FP64
 
     def c(self) -> CParams3:
         return CParams3(self.nx, self.ny, self.nz, self.tau, self.kappa, self.beta, self.rho_l,
-                        self.rho_g, self.rho0, self.scheme)
+                        self.rho_g, self.rho0, self.scheme, self.precision)
 
 
 class Solver3:
-    """One D3Q19 lattice (FP64) on the current CUDA device (wblbe3_*)."""
+    """One D3Q19 lattice (FP64 or FP32-shifted) on the current CUDA device
+    (wblbe3_*)."""
 
     def __init__(self, params: Params3, stream=None):
         import torch

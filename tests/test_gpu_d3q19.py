@@ -155,3 +155,88 @@ def test_d3q19_spherical_droplet_young_laplace():
     assert not st["nonfinite"] and abs(st["mass_drift_rel"]) < 1e-12
     assert abs(ratio - 1.0) < 0.05, ratio
     assert rin > 1.0 and rout > 0.1
+
+
+def _run3(rho, n, precision, scheme, steps, tau=1.0, rho_g=0.1):
+    beta = eq.beta_for_width(0.01, 4.0, 1.0, rho_g)
+    g = wblbe.Solver3(wblbe.Params3(n, n, n, tau, 0.01, beta, 1.0, rho_g, 0.0, scheme,
+                                    precision))
+    g.init_rho(rho)
+    g.step(steps)
+    f = g.get_populations()
+    m, st = g.moments()
+    g.close()
+    return f, m, st
+
+
+@pytest.mark.parametrize("scheme,rho_g", [(wblbe.WELL_BALANCED, 0.1), (wblbe.STANDARD, 0.5)])
+def test_d3q19_fp32_shifted_against_fp64(scheme, rho_g):
+    """32^3 droplet (R = 8, W = 4, tau = 1.0), 400 steps, FP32-shifted
+    storage against the FP64 path (itself pinned to the oracle above):
+    populations within 2e-5 of max|f| (the bound of the 2D FP32 path), rho
+    and mu within 2e-5 of their scales, u within 2e-5 of max|u| + 1e-7, and
+    the FP32 mass within 1e-7 of its start."""
+    n = 32
+    rho = _droplet(n, 8.0, rho_g=rho_g)
+    f32, m32, s32 = _run3(rho, n, wblbe.FP32_SHIFTED, scheme, 400, rho_g=rho_g)
+    f64, m64, s64 = _run3(rho, n, wblbe.FP64, scheme, 400, rho_g=rho_g)
+    assert not s32["nonfinite"]
+    assert np.abs(f32 - f64).max() < 2e-5 * np.abs(f64).max()
+    assert np.abs(m32["rho"] - m64["rho"]).max() < 2e-5 * np.abs(m64["rho"]).max()
+    beta = eq.beta_for_width(0.01, 4.0, 1.0, rho_g)
+    assert np.abs(m32["mu"] - m64["mu"]).max() < 2e-5 * 2 * beta * (1.0 - rho_g) ** 3
+    assert np.abs(m32["u"] - m64["u"]).max() < 2e-5 * np.abs(m64["u"]).max() + 1e-7
+    assert abs(s32["mass_drift_rel"]) < 1e-7
+
+
+@pytest.mark.parametrize("scheme", [wblbe.WELL_BALANCED, wblbe.STANDARD])
+def test_d3q19_fp32_uniform_state_is_kept(scheme):
+    """A uniform state is a fixed point of both schemes.  In FP32-shifted
+    storage the well-balanced one keeps it bit for bit (its moving
+    populations are zero and every rounding remainder vanishes); the
+    standard one, whose moving populations w_i (rho - rho_ref) are rebuilt
+    every step, within float rounding and at rest."""
+    n = 12
+    rho = np.full((n, n, n), 0.37)
+    g = wblbe.Solver3(wblbe.Params3(n, n, n, 0.8, 0.01, 0.01, 1.0, 0.1, 0.0, scheme,
+                                    wblbe.FP32_SHIFTED))
+    g.init_rho(rho)
+    f0 = g.get_populations()
+    g.step(50)
+    f1 = g.get_populations()
+    m, st = g.moments()
+    g.close()
+    if scheme == wblbe.WELL_BALANCED:
+        assert np.array_equal(f0, f1)
+        assert st["umax"] == 0.0 and st["mass_drift_rel"] == 0.0
+    else:
+        assert np.abs(f1 - f0).max() < 1e-6 * np.abs(f0).max()
+        assert st["umax"] < 1e-7 and abs(st["mass_drift_rel"]) < 1e-6
+
+
+def test_d3q19_fp32_droplet_follows_fp64():
+    """64^3 droplet R = 20 (W = 4, ratio 10, tau = 1.0, WB), 10000 steps in
+    both precisions: the inner and outer bulk densities within 2e-6 of
+    FP64's, the Laplace jump (2D-style Delta p R / (2 sigma)) within 1e-3 of
+    FP64's, the mass within 1e-6, max|u| within 5 % of FP64's."""
+    n, R = 64, 20.0
+    rho = _droplet(n, R)
+    _, m32, s32 = _run3(rho, n, wblbe.FP32_SHIFTED, wblbe.WELL_BALANCED, 10000)
+    _, m64, s64 = _run3(rho, n, wblbe.FP64, wblbe.WELL_BALANCED, 10000)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - n // 2) ** 2 + (y - n // 2) ** 2 + (z - n // 2) ** 2)
+    inner, outer = r < R / 2, r > R + 10
+    beta = eq.beta_for_width(0.01, 4.0, 1.0, 0.1)
+    sigma = eq.surface_tension(0.01, beta, 1.0, 0.1)
+
+    def jump(m):
+        rin, rout = m["rho"][inner].mean(), m["rho"][outer].mean()
+        return rin, rout, (eq.p0(rin, beta, 1.0, 0.1) - eq.p0(rout, beta, 1.0, 0.1)) * R / (2 * sigma)
+
+    i32, o32, j32 = jump(m32)
+    i64, o64, j64 = jump(m64)
+    assert not s32["nonfinite"]
+    assert abs(i32 - i64) < 2e-6 and abs(o32 - o64) < 2e-6
+    assert abs(j32 - j64) < 1e-3
+    assert abs(s32["mass_drift_rel"]) < 1e-6
+    assert abs(s32["umax"] - s64["umax"]) < 0.05 * s64["umax"]
