@@ -1,5 +1,6 @@
 // The three-dimensional form of the well-balanced LBE (and of the standard
-// LBE) on the D3Q19 lattice, FP64: the wblbe3_* half of include/wblbe.h.
+// LBE) on the D3Q19 lattice, in FP64 or FP32-shifted storage: the wblbe3_*
+// part of include/wblbe.h.
 //
 // The paper builds the well-balanced scheme in D dimensions (Sec. III): the
 // equilibrium of Eq. mFeq, F = -rho grad(mu) (Eq. mF) and the forcing term of
@@ -10,17 +11,19 @@
 // grad(phi) = 3 sum_i w_i c_i phi(x + c_i) and
 // lap(phi) = 6 sum_i w_i (phi(x + c_i) - phi(x)).
 //
-// One step is three kernels on the caller's stream (FP64 arithmetic is the
-// limit here, not memory traffic):
+// One step is three kernels on the caller's stream (in FP64 the FP64 pipe is
+// the limit, not memory traffic; in FP32 the traffic is):
 //   d3_density:   rho(x) = sum_i P_i(x - c_i)           (pull, Eq. rhoU)
 //   d3_chem_pot:  mu = mu_0(rho) - kappa lap(rho)        (Sec. II)
 //   d3_collide:   the pulled populations, grad rho and grad mu, the force,
 //                 u, the equilibrium and forcing terms, and the BGK update
 //                 (Eq. D2Q9), stored at x for the next pull.
 // Layout: nineteen planes P_i[(z ny + y) pitch + x], pitch = nx rounded up
-// to 128 bytes, two buffers (ping-pong); the planes hold f_i - s_i with the
-// well-balanced rho0 vector s_0 = -(1 - w_0) rho0, s_i = w_i rho0 (0 for the
-// standard scheme), which the update carries unchanged.
+// to 16 elements, two buffers (ping-pong); the planes hold f_i - s_i, with
+// s_i the well-balanced rho0 vector s_0 = -(1 - w_0) rho0, s_i = w_i rho0 (0
+// for the standard scheme), plus in FP32 the scheme's rest equilibrium at
+// rho_ref = rho_g; the update carries the shift unchanged.  The density and
+// chemical-potential fields hold rho - rho_ref and mu in the storage type.
 #include <cuda_runtime.h>
 
 #include <cmath>
