@@ -406,14 +406,15 @@ int64_t wblbe_slabs_kernel_launches(wblbe_slabs_handle h);
 wblbe_status wblbe_slabs_destroy(wblbe_slabs_handle h);
 const char* wblbe_slabs_last_error(wblbe_slabs_handle h);
 
-/* ---- three dimensions: D3Q19, FP64 ----------------------------------------
+/* ---- three dimensions: D3Q19, FP64 or FP32-shifted -------------------------
  * The paper's construction is written for D dimensions (Eq. mFeq, Eq. mF and
  * Eq. mFi, whose isotropic term carries D; Sec. V notes it carries over to
  * other LBE models).  These entry points run it, and the standard scheme, on
  * the D3Q19 lattice (D = 3, cs^2 = 1/3, weights 1/3, 1/18, 1/36) with the
  * isotropic central stencils grad(phi) = 3 sum_i w_i c_i phi(x + c_i),
  * lap(phi) = 6 sum_i w_i (phi(x + c_i) - phi(x)), periodic in x, y, z, in
- * float64.  Direction order (rest, axes, edges in opposite pairs):
+ * float64 or float32-shifted storage (below).  Direction order (rest, axes,
+ * edges in opposite pairs):
  *   c0 = (0,0,0); c1..c6 = (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1);
  *   c7..c18 = (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
  *             (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1).
